@@ -1,0 +1,327 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each check uses an independent
+computation (exhaustive search, a transfer-matrix DP, a closed form, values
+printed in the paper) or an invariant the paper proves.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# ------------------------------------------------------------------ Eq. 3
+def test_eq3_worked_example(orc):
+    g = _gold("eq3_example.json")
+    got = [orc.project_index(g["out_dom"], g["phi"], r) for r in g["r_out"]]
+    assert got == g["r_in"]
+
+
+def test_eq3_is_mixed_radix_projection(orc):
+    # closed form: r_in is the row-major index of the projected digits
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        m = int(rng.integers(1, 6))
+        dom = rng.integers(1, 5, size=m).tolist()
+        keep = sorted(set(rng.choice(m - 1, size=int(rng.integers(0, m)), replace=True).tolist())) if m > 1 else []
+        phi = keep + [m - 1]
+        for r in range(int(np.prod(dom))):
+            digits = np.unravel_index(r, dom)
+            want = np.ravel_multi_index([digits[p] for p in phi], [dom[p] for p in phi])
+            assert orc.project_index(dom, phi, r) == want
+
+
+# ------------------------------------------------------------- brute force
+def test_bruteforce_unary_closed_form(orc):
+    # with unary functions only, the optimum is the sum of the unary minima
+    rng = np.random.default_rng(2)
+    dom = np.array([3, 2, 4], dtype=np.int32)
+    scopes = [np.array([v], dtype=np.int32) for v in range(3)] + [np.array([1], dtype=np.int32)]
+    tables = [rng.integers(0, 50, size=int(dom[s[0]])) for s in scopes]
+    inst = synth.Instance("unary", dom, scopes, tables, "int", 1 << 30)
+    best, sig = orc.bruteforce(inst)
+    want = tables[0].min() + (tables[1] + tables[3]).min() + tables[2].min()
+    assert best == want
+    assert orc.evaluate(inst, sig) == best
+
+
+def test_eval_matches_numpy_broadcast(orc):
+    # Eq. 1 on every assignment against a dense numpy evaluation
+    for seed in range(5):
+        inst = synth.random_small(seed, n=4, dmax=3, n_funcs=6)
+        dense = np.zeros(tuple(int(d) for d in inst.dom))
+        for s, t in zip(inst.scopes, inst.tables):
+            shape = [1] * inst.n
+            for v in s:
+                shape[v] = int(inst.dom[v])
+            arr = np.asarray(t, dtype=np.float64).reshape([int(inst.dom[v]) for v in s])
+            order = np.argsort(s)
+            arr = np.transpose(arr, order).reshape(shape) if len(s) else arr.reshape(shape)
+            dense = dense + arr
+        dense = np.minimum(dense, inst.top_k)
+        for a in itertools.product(*[range(int(d)) for d in inst.dom]):
+            assert orc.evaluate(inst, np.array(a)) == dense[a]
+
+
+# ------------------------------------------------------ worked example (Sec. 2)
+def _structure(run):
+    return [{"var": int(t.var), "sep": [int(x) for x in t.sep], "inputs": sorted(int(x) for x in t.inputs)}
+            for t in run.tasks]
+
+
+def test_paper_example_structure(orc):
+    g = _gold("paper_example_structure.json")
+    inst = synth.paper_example()
+    order = np.array(g["elimination_order"], dtype=np.int32)
+    assert orc.induced_width(inst, order) == g["induced_width"]
+    be = orc.eliminate(inst, order, "be")
+    assert _structure(be) == g["be_tasks"]
+    mbe = orc.eliminate(inst, order, "sep", 1)
+    assert _structure(mbe) == g["mbe_z1_tasks"]
+    # MBE gives a lower bound, its assignment an upper bound (Section 2.2)
+    assert mbe.bound <= be.bound <= mbe.cost
+    assert be.cost == be.bound
+
+
+# ------------------------------------------------------ BE = exhaustive optimum
+@pytest.mark.parametrize("cost_type", ["int", "real"])
+@pytest.mark.parametrize("seed", range(12))
+def test_be_equals_bruteforce(orc, seed, cost_type):
+    inst = synth.random_small(seed, n=6, dmax=3, n_funcs=9, max_arity=3, cost_type=cost_type)
+    best, _ = orc.bruteforce(inst)
+    rng = np.random.default_rng(seed)
+    orders = [orc.minfill(inst)[0], np.arange(inst.n), rng.permutation(inst.n)]
+    for order in orders:
+        run = orc.eliminate(inst, order, "be")
+        if cost_type == "int":
+            assert run.bound == best
+            assert run.cost == best
+        else:
+            assert run.bound == pytest.approx(best, rel=1e-12, abs=1e-12)
+            assert run.cost == pytest.approx(best, rel=1e-12, abs=1e-12)
+        assert orc.evaluate(inst, run.sigma) == run.cost
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_mbe_bounds_and_exactness(orc, seed):
+    inst = synth.random_small(seed + 100, n=7, dmax=3, n_funcs=10, max_arity=3)
+    best, _ = orc.bruteforce(inst)
+    order, w = orc.minfill(inst)
+    be = orc.eliminate(inst, order, "be")
+    for mode in ("sep", "joint", "log2"):
+        for z in range(0, 8):
+            run = orc.eliminate(inst, order, mode, z)
+            assert run.bound <= best <= run.cost
+            assert orc.evaluate(inst, run.sigma) == run.cost
+    # once the bound admits every bucket, MBE is BE: identical tables
+    exact = orc.eliminate(inst, order, "sep", w)
+    assert _structure(exact) == _structure(be)
+    for a, b in zip(exact.tasks, be.tasks):
+        assert np.array_equal(a.out, b.out) and np.array_equal(a.arg, b.arg)
+    assert exact.bound == best
+
+
+def test_saturation_at_top(orc):
+    # every joint entry sums past k: the optimum saturates to k and argmin is 0
+    k = 100
+    dom = np.array([2, 2], dtype=np.int32)
+    scopes = [np.array([0, 1], dtype=np.int32), np.array([1], dtype=np.int32)]
+    tables = [np.array([60, 70, 80, 90]), np.array([50, 45])]
+    inst = synth.Instance("sat", dom, scopes, tables, "int", k)
+    run = orc.eliminate(inst, np.array([1, 0]), "be")
+    assert run.bound == k
+    assert [int(x) for x in run.tasks[0].out] == [k, k]
+    assert [int(x) for x in run.tasks[0].arg] == [0, 0]
+    assert list(run.sigma) == [0, 0]
+
+
+def test_argmin_first_minimum(orc):
+    dom = np.array([3], dtype=np.int32)
+    inst = synth.Instance("tie", dom, [np.array([0], dtype=np.int32)], [np.array([5, 2, 2])], "int", 1 << 30)
+    run = orc.eliminate(inst, np.array([0]), "be")
+    assert run.bound == 2 and int(run.tasks[0].arg[0]) == 1 and run.sigma[0] == 1
+
+
+# --------------------------------------------- the two bucket formulations agree
+def _to_joint(inst, f_scope, table, joint):
+    """Re-lay a table row-major over its scope's subsequence of `joint`."""
+    f_scope = [int(x) for x in f_scope]
+    arr = np.asarray(table, dtype=np.float64).reshape([int(inst.dom[v]) for v in f_scope])
+    keep = [v for v in joint if v in f_scope]
+    return np.transpose(arr, [f_scope.index(v) for v in keep]).reshape(-1), keep
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_eq3_bucket_matches_assignment_form(orc, seed):
+    inst = synth.random_small(seed + 7, n=6, dmax=3, n_funcs=9, with_constant=False)
+    order, _ = orc.minfill(inst)
+    run = orc.eliminate(inst, order, "sep", 2)
+    funcs = {j: (inst.scopes[j], inst.tables[j]) for j in range(inst.n_funcs)}
+    for t, T in enumerate(run.tasks):
+        joint = [int(x) for x in T.sep] + [T.var]
+        tabs, poss = [], []
+        for i in T.inputs:
+            s, tab = funcs[int(i)]
+            flat, keep = _to_joint(inst, s, tab, joint)
+            tabs.append(flat)
+            poss.append([joint.index(v) for v in keep[:-1]])
+            assert keep[-1] == T.var
+        out, arg = orc.util_bucket([int(inst.dom[v]) for v in T.sep], int(inst.dom[T.var]),
+                                   tabs, poss, True, inst.top_k)
+        assert np.array_equal(out, T.out) and np.array_equal(arg, T.arg)
+        funcs[inst.n_funcs + t] = (T.sep, T.out)
+
+
+# ------------------------------------------------- grids: transfer-matrix DP
+def _grid_dp(inst, rows, cols, d):
+    """Row-by-row dynamic programme over all d**cols row states: an algorithm
+    independent of variable elimination."""
+    un = np.zeros((rows * cols, d))
+    h = {}
+    for s, t in zip(inst.scopes, inst.tables):
+        s = [int(x) for x in s]
+        if len(s) == 1:
+            un[s[0]] += t
+        else:
+            h[tuple(s)] = np.asarray(t, dtype=np.float64).reshape(d, d)
+    states = np.array(list(itertools.product(range(d), repeat=cols)))
+    def row_cost(r):
+        c = np.zeros(len(states))
+        for j in range(cols):
+            v = r * cols + j
+            c += un[v][states[:, j]]
+            if j + 1 < cols:
+                c += h[(v, v + 1)][states[:, j], states[:, j + 1]]
+        return c
+    best = row_cost(0)
+    for r in range(1, rows):
+        trans = np.zeros((len(states), len(states)))
+        for j in range(cols):
+            v = (r - 1) * cols + j
+            trans += h[(v, v + cols)][states[:, j][:, None], states[:, j][None, :]]
+        best = (best[:, None] + trans).min(axis=0) + row_cost(r)
+    return best.min()
+
+
+def test_config0_transfer_matrix(orc):
+    for seed in range(3):
+        inst = synth.config_instance(0, seed)
+        order, w = orc.minfill(inst)
+        assert w == 4
+        run = orc.eliminate(inst, order, "be")
+        assert run.bound == _grid_dp(inst, 4, 5, 4)
+        assert run.cost == run.bound
+
+
+def test_grid_natural_order_width(orc):
+    # row-major elimination of an r x c grid keeps c variables on the frontier
+    for r, c in [(4, 5), (12, 12), (3, 7)]:
+        inst = synth.grid_wcsp(r, c, 2, 0, unary=False)
+        assert orc.induced_width(inst, np.arange(r * c)) == c
+
+
+def test_minfill_small_graphs(orc):
+    # a star has width 1 (leaves go first), a 5-cycle width 2
+    star = synth.Instance("star", np.full(5, 2, np.int32),
+                          [np.array([0, v], np.int32) for v in range(1, 5)],
+                          [np.zeros(4, np.int64)] * 4, "int", 1 << 30)
+    order, w = orc.minfill(star)
+    assert w == 1 and int(order[-1]) in (0, 4) and sorted(order.tolist()) == list(range(5))
+    cyc = synth.Instance("cyc", np.full(5, 2, np.int32),
+                         [np.array(sorted((v, (v + 1) % 5)), np.int32) for v in range(5)],
+                         [np.zeros(4, np.int64)] * 5, "int", 1 << 30)
+    order, w = orc.minfill(cyc)
+    assert w == 2 and int(order[0]) == 0
+
+
+# ------------------------------------------------------ components (Sec. 6.2)
+def test_components_add_up(orc):
+    a = synth.random_small(31, n=5, dmax=3, n_funcs=6, with_constant=False)
+    b = synth.random_small(32, n=4, dmax=3, n_funcs=5, with_constant=False)
+    a.top_k = b.top_k = 10**6
+    u = synth.disjoint_union(a, b)
+    ra = orc.eliminate(a, orc.minfill(a)[0], "be").bound
+    rb = orc.eliminate(b, orc.minfill(b)[0], "be").bound
+    ru = orc.eliminate(u, orc.minfill(u)[0], "be").bound
+    assert ru == ra + rb
+
+
+# --------------------------------------------------------- DPOP (Section 4)
+def _ancestors(parent, v):
+    out = []
+    v = int(parent[v])
+    while v >= 0:
+        out.append(v)
+        v = int(parent[v])
+    return out
+
+
+def _descendants(parent, v):
+    n = len(parent)
+    return [u for u in range(n) if v in _ancestors(parent, u)]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_dpop_separators(orc, seed):
+    inst = synth.dcop_random(seed, n_range=(8, 14), d_range=(2, 3))
+    for parent in (orc.dfs_pseudotree(inst), inst.parent):
+        # every constraint joins an ancestor and a descendant (Definition 2)
+        for s in inst.scopes:
+            a, b = int(s[0]), int(s[1])
+            assert a in _ancestors(parent, b) or b in _ancestors(parent, a)
+        order = orc.pseudotree_order(inst, parent)
+        run = orc.eliminate(inst, order, "be")
+        linked = {v: set() for v in range(inst.n)}
+        for s in inst.scopes:
+            linked[int(s[0])].add(int(s[1]))
+            linked[int(s[1])].add(int(s[0]))
+        for T in run.tasks:
+            sub = [T.var] + _descendants(parent, T.var)
+            want = {a for a in _ancestors(parent, T.var) if any(a in linked[u] for u in sub)}
+            assert set(int(x) for x in T.sep) == want
+        best, _ = orc.bruteforce(inst) if np.prod(inst.dom.astype(float)) < 2e5 else (run.bound, None)
+        assert run.bound == best
+
+
+def test_dfs_pseudotree_root_and_order(orc):
+    # root = highest degree; the post-order lists every node after its children
+    inst = synth.dcop_random(3, n_range=(12, 12), d_range=(2, 2))
+    par = orc.dfs_pseudotree(inst)
+    deg = np.zeros(inst.n, int)
+    for s in inst.scopes:
+        deg[s] += 1
+    roots = [v for v in range(inst.n) if par[v] == -1]
+    assert roots[0] == int(np.argmax(deg))
+    order = orc.pseudotree_order(inst, par)
+    pos = {int(v): i for i, v in enumerate(order)}
+    for v in range(inst.n):
+        if par[v] >= 0:
+            assert pos[v] < pos[int(par[v])]
+
+
+# ----------------------------------------------------- MPE (Section 3)
+def test_mpe_log_domain_bruteforce(orc):
+    inst = synth.bayes_net_mpe(9, seed=4)
+    best, sig = orc.bruteforce(inst)
+    # the max-product optimum in probability space, by direct products
+    pbest = 0.0
+    for a in itertools.product(*[range(int(d)) for d in inst.dom]):
+        p = 1.0
+        for s, t in zip(inst.scopes, inst.tables):
+            idx = np.ravel_multi_index([a[v] for v in s], [int(inst.dom[v]) for v in s])
+            p *= np.exp(-t[idx])
+        pbest = max(pbest, p)
+    assert best == pytest.approx(-np.log(pbest), rel=1e-12)
+    run = orc.eliminate(inst, orc.minfill(inst)[0], "be")
+    assert run.bound == pytest.approx(best, rel=1e-12)
