@@ -1,0 +1,295 @@
+/*
+ * gpube.h - C ABI of the GB300 UTIL-table library.
+ *
+ * The library computes the bucket functions (UTIL tables) of Bucket
+ * Elimination (BE, Algorithm 1), Mini-Bucket Elimination (MBE, Algorithm 2)
+ * and the UTIL phase of DPOP (Section 4.1) on one NVIDIA GB300 GPU, and the
+ * value-assignment (VALUE) phase that follows them, for problems stated as in
+ * Sections 2-4 of arXiv 1608.05288:
+ *
+ *   WCSP <X, D, C>          (Section 2): integer costs in [0, top_k]; top_k
+ *                           stands for "infinity" (not allowed) and sums
+ *                           saturate at it;
+ *   Bayesian network / MPE  (Section 3): costs -log p in fp32, p = 0 -> +inf;
+ *                           max-product becomes min-sum;
+ *   DCOP <X, D, C, A, alpha> (Section 4): one variable per agent; the UTIL
+ *                           messages are BE's bucket functions along the
+ *                           post-order of a DFS pseudo-tree.
+ *
+ * Conventions shared by every call
+ *   - Variables are 0..n_vars-1.  An elimination order lists variables in the
+ *     order they are eliminated (order[0] first).
+ *   - A cost table is row-major over its scope as listed: the first scope
+ *     variable varies slowest (the lexicographic rows of the bucket-table,
+ *     Section 6.1).
+ *   - A bucket function's scope is its separator sorted by descending
+ *     elimination position; its eliminated variable, when present in a table,
+ *     is last (Section 6.2).
+ *   - Ties in min / argmin go to the lowest domain value.
+ *   - Return codes: 0 on success, or a negative GPUBE_E* status; no call
+ *     aborts the process.  wcsp_last_error() describes the last failure of
+ *     the calling thread.
+ *   - Device memory: either the caller passes an arena (a device pointer and
+ *     its size, e.g. from torch) or, when the arena is NULL, the library
+ *     allocates one itself with cudaMalloc and frees it with the state.
+ *   - Streams: every GPU call runs on the caller's cudaStream_t (passed as
+ *     void*; NULL = the legacy default stream).
+ */
+#ifndef GPUBE_H
+#define GPUBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define GPUBE_OK 0
+#define GPUBE_EINVAL (-22)     /* malformed problem or argument              */
+#define GPUBE_ENOMEM (-12)     /* arena or budget too small / host OOM       */
+#define GPUBE_ETIMEDOUT (-110) /* a bounded device-side wait gave up         */
+#define GPUBE_ECUDA (-1000)    /* a CUDA runtime call failed                 */
+#define GPUBE_ENODEV (-19)     /* no usable CUDA device                      */
+#define GPUBE_EAGAIN (-11)     /* serving: request not admitted yet / busy   */
+
+/* ------------------------------------------------------------ enumerations */
+enum wcsp_cost_type {
+    WCSP_INT32_SAT = 0, /* int32 costs in [0, top_k], saturating sum (Section 2) */
+    WCSP_FP32_LOG = 1   /* fp32 -log p costs, +inf allowed (Section 3)           */
+};
+
+enum gpube_order_kind {
+    GPUBE_ORDER_MINFILL = 0,    /* greedy min-fill; ties: fewest neighbours, lowest id   */
+    GPUBE_ORDER_BEST = 1,       /* min-fill or the natural order 0..n-1, whichever has the
+                                   smaller induced width (ties keep min-fill)            */
+    GPUBE_ORDER_GIVEN = 2,      /* solve_opts.order                                       */
+    GPUBE_ORDER_NATURAL = 3,    /* 0, 1, ..., n-1                                         */
+    GPUBE_ORDER_PSEUDOTREE = 4  /* post-order of solve_opts.parent, or of the library's DFS
+                                   pseudo-tree when parent is NULL (Section 6.2)          */
+};
+
+enum gpube_ibound_mode {
+    GPUBE_IB_SEP_VARS = 0,    /* |scope(mini-bucket) \ {x_i}| <= i_bound                 */
+    GPUBE_IB_JOINT_VARS = 1,  /* |scope(mini-bucket)| <= i_bound (Algorithm 2 line 3)     */
+    GPUBE_IB_LOG2_ENTRIES = 2 /* product of the mini-bucket's domains <= 2^i_bound        */
+};
+
+enum gpube_kind { GPUBE_KIND_BE = 0, GPUBE_KIND_MBE = 1, GPUBE_KIND_DPOP = 2 };
+
+/* ------------------------------------------------------------------ structs */
+
+/* A problem (Sections 2-4).  All arrays are host memory owned by the caller;
+ * wcsp_load copies them.  Function j has scope scope[scope_off[j] ..
+ * scope_off[j+1]) (distinct variables; an empty scope is a constant) and
+ * table costs[tab_off[j] .. tab_off[j+1]), whose length must be the product
+ * of the scope's domain sizes.  costs points to int32 (WCSP_INT32_SAT:
+ * values in [0, top_k]; larger values are read as top_k, negative values are
+ * EINVAL) or to float (WCSP_FP32_LOG: values >= 0 or +inf). */
+typedef struct wcsp_desc {
+    int32_t n_vars;
+    const int32_t *dom;       /* [n_vars], each 1..255                    */
+    int32_t n_funcs;
+    const int32_t *scope_off; /* [n_funcs + 1]                            */
+    const int32_t *scope;     /* [scope_off[n_funcs]]                     */
+    const int64_t *tab_off;   /* [n_funcs + 1], in entries                */
+    const void *costs;        /* int32_t* or float*                       */
+    int32_t cost_type;        /* enum wcsp_cost_type                      */
+    int32_t top_k;            /* WCSP top cost k, 1..2^31-1 (int type)    */
+} wcsp_desc;
+
+/* Options of a solve.  Initialise with solve_opts_init(). */
+typedef struct solve_opts {
+    int32_t order_kind;        /* enum gpube_order_kind                                  */
+    const int32_t *order;      /* [n] host, for GPUBE_ORDER_GIVEN                        */
+    const int32_t *parent;     /* [n] host pseudo-tree (-1 = root) for ORDER_PSEUDOTREE  */
+    int32_t ibound_mode;       /* enum gpube_ibound_mode (MBE)                           */
+    int32_t batched;           /* 1: one persistent launch per elimination-tree level;
+                                  0: one launch per (mini-)bucket                        */
+    int32_t use_graph;         /* 1: capture the launch sequence once in a CUDA graph    */
+    int32_t block_threads;     /* UTIL kernel CTA size (64..1024, multiple of 32); 0 = auto */
+    int32_t rows_per_item;     /* separator rows of one work item per thread; 0 = auto  */
+    int32_t lo_target;         /* minimum extent of a work item's inner row block; 0 = auto */
+    int32_t stage_max_entries; /* tables up to this many entries are staged in shared
+                                  memory; 0 = auto, -1 = never stage                    */
+    void *arena;               /* device memory for all tables, or NULL                 */
+    size_t arena_bytes;
+    void *stream;              /* cudaStream_t, NULL = legacy default stream            */
+    const char *autotune_cache;/* file for tuned launch parameters, or NULL             */
+    int32_t device;            /* CUDA device ordinal                                    */
+} solve_opts;
+
+/* Result of a solve.  assignment, when non-NULL, is caller-owned host memory
+ * of n_vars int32 and receives the VALUE-phase assignment.  For WCSP_INT32_SAT
+ * the costs are integers held exactly in double; top_k means infeasible. */
+typedef struct solve_result {
+    double bound;           /* sum of the root constants: the optimum (BE, DPOP) or a
+                               lower bound (MBE, Section 2.2)                       */
+    double cost;            /* Eq. 1 cost of the returned assignment (an upper bound
+                               for MBE)                                             */
+    int32_t *assignment;    /* in: caller buffer or NULL                            */
+    int32_t induced_width;  /* largest separator of the run                         */
+    int32_t n_tasks;        /* (mini-)buckets computed                              */
+    int32_t n_levels;       /* elimination-tree levels                              */
+    int32_t n_launches;     /* UTIL kernel launches of one run                      */
+    int64_t util_entries;   /* sum over tasks of separator rows x |D_x| (joint rows) */
+    int64_t alg_bytes;      /* 4 x input entries + 5 x output entries, over tasks   */
+    double plan_ms;         /* host planning time                                   */
+    double util_ms;         /* device time of the UTIL phase (CUDA events)          */
+    double value_ms;        /* device time of the VALUE phase                       */
+} solve_result;
+
+/* Planning summary, available right after util_plan (no GPU needed). */
+typedef struct gpube_plan_info {
+    int32_t n_vars, n_tasks, n_levels, induced_width;
+    int64_t util_entries, out_entries, in_entries, alg_bytes;
+    size_t arena_bytes;       /* device memory one state needs                  */
+    size_t peak_live_bytes;   /* its part that is live at the same time         */
+    int32_t max_sep;          /* largest separator                              */
+    int32_t max_inputs;       /* most functions in one (mini-)bucket            */
+} gpube_plan_info;
+
+/* One planned (mini-)bucket, for inspection and tests (no GPU needed).
+ * sep and inputs are caller buffers of at least n_vars and
+ * (max_inputs of gpube_plan_info) entries.  Input ids: original functions
+ * are 0..n_funcs-1; the output of task t has id n_funcs + t. */
+typedef struct gpube_task_info {
+    int32_t var, level, n_sep, n_inputs;
+    int64_t rows;           /* separator rows = entries of the output table */
+    int32_t *sep;           /* out: separator, descending elimination position */
+    int32_t *inputs;        /* out: input ids, in kernel input order */
+} gpube_task_info;
+
+typedef struct wcsp wcsp;             /* opaque, library-owned problem         */
+typedef struct util_state util_state; /* opaque, library-owned plan + tables    */
+
+/* ----------------------------------------------------------- problem calls */
+
+/* Copy and validate a problem (Sections 2-4).  EINVAL on a malformed
+ * description (bad domain, repeated scope variable, wrong table length,
+ * negative cost, ...).  The caller keeps ownership of d's arrays. */
+int wcsp_load(const wcsp_desc *d, wcsp **out);
+void wcsp_free(wcsp *w);
+const char *wcsp_last_error(void);
+void solve_opts_init(solve_opts *o);
+
+/* ------------------------------------------------------ one-call solvers */
+
+/* Bucket Elimination (Algorithm 1): UTIL phase on the GPU along the order of
+ * opts, root reduction, VALUE phase (argmin lookups), result to the host. */
+int be_solve(wcsp *w, const solve_opts *opts, solve_result *res);
+
+/* Mini-Bucket Elimination (Algorithm 2) with bound i_bound read in
+ * opts->ibound_mode.  res->bound is the lower bound; the assignment picks,
+ * per variable, the first argmin of the sum of all functions of its bucket. */
+int mbe_solve(wcsp *w, int32_t i_bound, const solve_opts *opts, solve_result *res);
+
+/* DPOP UTIL phase (Section 4.1) along the pseudo-tree parent[] (host, n
+ * entries, -1 = root; NULL = the library's DFS pseudo-tree).  Every
+ * constraint must join an ancestor and a descendant of parent[] (EINVAL
+ * otherwise).  On success *out holds the UTIL messages on the device; call
+ * value_propagate for the VALUE phase and util_state_free afterwards. */
+int dpop_util(wcsp *w, const int32_t *parent, const solve_opts *opts, util_state **out);
+
+/* VALUE phase (Algorithm 1/2 value assignment, DPOP VALUE propagation) over a
+ * state whose UTIL phase has run.  assignment (host, n) may be NULL. */
+int value_propagate(util_state *s, int32_t *assignment, solve_result *res);
+
+void util_state_free(util_state *s);
+
+/* ------------------------------------------------------ staged interface */
+
+/* Host planning only (ordering, buckets, mini-bucket partition, levels,
+ * kernel work decomposition); no GPU needed.  kind: enum gpube_kind;
+ * i_bound is used by GPUBE_KIND_MBE; parent by GPUBE_KIND_DPOP. */
+int util_plan(wcsp *w, int32_t kind, int32_t i_bound, const int32_t *parent,
+              const solve_opts *opts, util_state **out);
+int util_plan_info(const util_state *s, gpube_plan_info *info);
+int util_task_info(const util_state *s, int32_t t, gpube_task_info *info);
+/* The elimination order of the plan (host, n entries). */
+int util_order(const util_state *s, int32_t *order);
+
+/* Bind device memory (arena == NULL: the library allocates) and upload the
+ * tables and the kernel plan.  Must precede util_run. */
+int util_bind(util_state *s, void *arena, size_t arena_bytes, void *stream);
+
+/* Run the UTIL phase on the bound stream (asynchronous: returns after the
+ * launches are queued).  Re-runnable: every run recomputes all tables. */
+int util_run(util_state *s);
+
+/* Queue the VALUE phase (root reduction, assignment, Eq. 1 cost of the
+ * assignment) on the device; value_propagate = value_launch + copy back. */
+int util_value_launch(util_state *s);
+
+/* Wait for the bound stream and report a device-side status (ETIMEDOUT if a
+ * bounded wait gave up). */
+int util_sync(util_state *s);
+
+/* Copy one task's output (cost table and argmin table, rows entries each) to
+ * host buffers (either may be NULL); synchronous. */
+int util_fetch_table(util_state *s, int32_t t, void *cost_host, uint8_t *arg_host);
+
+/* Measure candidate launch parameters (CTA size, rows per item) on this
+ * state's own UTIL phase, keep the fastest, and record them in
+ * opts.autotune_cache when given.  Writes the chosen values to *threads and
+ * *rows_per_item (either may be NULL). */
+int util_autotune(util_state *s, int32_t *threads, int32_t *rows_per_item);
+
+/* Device time in ms of the last util_run / VALUE phase (after util_sync). */
+int util_last_times(util_state *s, double *util_ms, double *value_ms);
+
+/* ---------------------------------------------------- single-bucket kernel */
+
+/* One (mini-)bucket on the GPU: the fused aggregation + elimination of
+ * Section 6.3-6.4 (Procedures Gpu::Aggregate, Gpu::Eliminate), also writing
+ * the first argmin.  The joint scope is m separator variables (domains
+ * sep_dom[0..m-1], host) followed by the eliminated variable (domain d).
+ * Input i is a device table row-major over its scope: the separator
+ * variables at positions in_pos[in_pos_off[i] .. in_pos_off[i+1]) (host,
+ * ascending, each in 0..m-1) followed by the eliminated variable.  in_tables
+ * (host array of n_in device pointers, 16-byte aligned) point to int32
+ * (WCSP_INT32_SAT) or float (WCSP_FP32_LOG) data.  out (device, rows
+ * entries of the same type) and arg (device, rows bytes) receive the
+ * bucket function and its argmin, rows = product of sep_dom.  Scratch
+ * (plan tables) comes from a per-device buffer the library keeps and grows
+ * with cudaMalloc.  Asynchronous on stream. */
+int util_bucket(int32_t cost_type, int32_t top_k, int32_t m, const int32_t *sep_dom, int32_t d,
+                int32_t n_in, const void *const *in_tables, const int32_t *in_pos_off,
+                const int32_t *in_pos, void *out, uint8_t *arg, void *stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/* A continuous-batching server for streams of problems (DCOP or WCSP) on one
+ * GPU.  Requests are admitted while their device-memory need (from the plan,
+ * before any allocation) fits in budget_bytes and a slot is free; the
+ * elimination-tree levels of all admitted requests are merged into shared
+ * persistent launches, so requests that arrive while others run join the
+ * next launch.  The arena (device, arena_bytes >= budget_bytes) is the
+ * caller's; NULL = the library allocates budget_bytes. */
+typedef struct gpube_server gpube_server;
+
+int srv_create(size_t budget_bytes, int32_t max_slots, void *arena, size_t arena_bytes,
+               void *stream, gpube_server **out);
+/* Submit a problem: plans it (kind as in util_plan) and queues it; returns a
+ * request id >= 0 or a negative status (ENOMEM when it can never fit). */
+int64_t srv_submit(gpube_server *s, wcsp *w, int32_t kind, int32_t i_bound,
+                   const int32_t *parent, const solve_opts *opts);
+/* Advance the server by one iteration: admit what fits, launch one merged
+ * level step, retire finished requests.  Returns the number of requests
+ * still in flight or queued. */
+int srv_step(gpube_server *s);
+/* Result of a finished request: 0 with res filled (assignment copied when
+ * non-NULL), EAGAIN if not finished. */
+int srv_result(gpube_server *s, int64_t id, int32_t *assignment, solve_result *res);
+/* Host times of a finished request (seconds on the server's monotonic
+ * clock): submit, admit, done. */
+int srv_times(gpube_server *s, int64_t id, double *t_submit, double *t_admit, double *t_done);
+int srv_stats(gpube_server *s, int64_t *launches, int64_t *peak_bytes, int64_t *max_inflight);
+void srv_free(gpube_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPUBE_H */

@@ -1,0 +1,164 @@
+// Host-side structures of the library: the loaded problem, the elimination
+// plan and the device state.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gpube.h"
+#include "gpube_dev.h"
+
+struct wcsp {
+    int32_t n = 0;
+    std::vector<int32_t> dom;
+    int32_t nf = 0;
+    std::vector<std::vector<int32_t>> scope;   // as given
+    std::vector<std::vector<int32_t>> itab;    // WCSP_INT32_SAT, clamped to top_k
+    std::vector<std::vector<float>> ftab;      // WCSP_FP32_LOG
+    int32_t cost_type = WCSP_INT32_SAT;
+    uint32_t top_k = 1u << 30;
+    std::vector<std::vector<int32_t>> adj;     // primal graph, sorted neighbour lists
+};
+
+namespace gpube {
+
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what);
+
+// A cost function during planning: an original constraint or a bucket
+// function.  Its canonical scope lists variables by descending elimination
+// position, so its bucket variable is last and has stride 1.
+struct Func {
+    std::vector<int32_t> scope;
+    int64_t size = 1;
+    int32_t task = -1;        // producing task, -1 for an original
+    size_t off = 0;           // arena byte offset of its cost table
+    const void *ext = nullptr;  // device table outside the arena (single-bucket calls)
+};
+
+// VALUE plan with arena offsets (pointers are patched in at bind time).
+struct ValueTermH {
+    size_t tab_off;
+    int32_t nv, var_off;
+};
+
+struct ValuePlanH {
+    std::vector<int32_t> lev_off, vorder;
+    std::vector<ValueVar> vinfo;
+    std::vector<ValueTermH> terms, evals;
+    std::vector<int32_t> vvars, vstrides;
+    std::vector<size_t> roots;
+    int32_t n_levels = 0;
+};
+
+struct Task {
+    int32_t var = -1, level = 0, d = 1;
+    std::vector<int32_t> sep;      // descending elimination position
+    std::vector<int32_t> inputs;   // function ids, kernel input order
+    int64_t rows = 1;              // separator rows (output entries)
+    size_t out_off = 0, arg_off = 0;
+    // work decomposition (see TaskDev)
+    int32_t L = 0;                 // lo digits (the lowest separator digits)
+    int64_t P_lo = 1, H = 1;
+    int32_t sa = 4, sb = 4;
+    std::vector<int32_t> hperm;    // hi digit indices, fastest first
+    size_t A_off = 0, B_off = 0;
+    void *ext_out = nullptr;       // caller's output tables (single-bucket calls)
+    uint8_t *ext_arg = nullptr;
+    std::vector<int32_t> stage_off;  // per input: shared-memory byte offset or -1
+    int32_t stage_bytes = 0;
+};
+
+struct Plan {
+    int32_t kind = GPUBE_KIND_BE;
+    int32_t i_bound = 0, ibound_mode = GPUBE_IB_SEP_VARS;
+    std::vector<int32_t> order, pos;
+    std::vector<Func> funcs;       // originals 0..nf-1, then task outputs nf+t
+    std::vector<Task> tasks;
+    int32_t n_levels = 0;
+    std::vector<int32_t> level_order;  // task ids sorted by (level, id)
+    std::vector<int32_t> level_off;    // [n_levels + 1] into level_order
+    int32_t width = 0, max_inputs = 0;
+    double const_sum = 0.0;
+    int64_t util_entries = 0, out_entries = 0, in_entries = 0;
+    int32_t lo_target = 2048;
+    int32_t stage_max_entries = 4096;
+    int32_t stage_max_bytes = 32768;
+    size_t peak_live_bytes = 0;
+    ValuePlanH value;
+};
+
+// Launch parameters of one run.
+struct LaunchCfg {
+    int32_t threads = 256;
+    int32_t rows_per_item = 16;
+};
+
+// planner (plan.cpp)
+const char *last_error();
+std::vector<int32_t> order_minfill(const wcsp &w, int32_t *width);
+int32_t induced_width(const wcsp &w, const std::vector<int32_t> &order);
+std::vector<int32_t> dfs_pseudotree(const wcsp &w);
+int pseudotree_order(const wcsp &w, const int32_t *parent, std::vector<int32_t> &order);
+int build_plan(const wcsp &w, int kind, int i_bound, const int32_t *parent, const solve_opts &o, Plan &P);
+void task_strides(const wcsp &w, const Plan &P, const Task &T, std::vector<int32_t> &st);
+void shape_tasks(const wcsp &w, Plan &P);
+
+// kernels (util_kernel.cu)
+cudaError_t launch_util(const LaunchDev &L, int cost_type, int grid, int threads, int smem, cudaStream_t s);
+int util_max_blocks_per_sm(int cost_type, int threads, int smem);
+cudaError_t launch_expand(const ExpandDev *tasks, const int64_t *prefix, int n_tasks, int64_t total,
+                          const int32_t *pool, int num_sms, cudaStream_t s);
+cudaError_t launch_value(const ValueDev &V, int cost_type, int smem, cudaStream_t s);
+
+}  // namespace gpube
+
+struct util_state;
+// api.cpp helpers used by the server
+namespace gpube {
+double now_ms();
+}
+
+// Byte offsets of the descriptor and value regions of a state's arena.
+struct DescLayout {
+    size_t taskdev = 0, indev = 0, prefix = 0, expand = 0, exp_prefix = 0, pool = 0;
+    size_t lev_off = 0, vorder = 0, vinfo = 0, terms = 0, vvars = 0, vstrides = 0, evals = 0, roots = 0;
+    size_t n_in = 0, n_prefix = 0, n_pool = 0;
+};
+
+struct util_state {
+    const wcsp *w = nullptr;
+    gpube::Plan plan;
+    gpube::LaunchCfg cfg;
+    solve_opts opts{};
+    bool batched = true, use_graph = true;
+    double plan_ms = 0.0;
+    // layout (byte offsets from the arena base)
+    size_t upload_bytes = 0;     // originals, packed first
+    size_t desc_off = 0, desc_bytes = 0;   // descriptor region (rebuilt per launch config)
+    size_t value_off = 0, value_bytes = 0; // value plan region
+    size_t work_off = 0;         // counters + status + result
+    size_t arena_bytes = 0;
+    // device binding
+    int device = 0;
+    unsigned char *base = nullptr;
+    bool owns_arena = false;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool bound = false, ran = false, value_ran = false;
+    bool sync_on_free = true;  // false when an owner (the server) knows the work is done
+    int num_sms = 0;
+    // launches of one run
+    std::vector<gpube::LaunchDev> launches;
+    std::vector<int32_t> launch_grid, launch_smem;
+    // value plan pointers
+    gpube::ValueDev vdev{};
+    int32_t value_smem = 0;
+    size_t counters_off = 0, status_off = 0, result_off = 0, sigma_off = 0;
+    std::vector<unsigned char> host_blob;  // staging for uploads
+    DescLayout dl;
+};

@@ -1,0 +1,515 @@
+// Host planning: elimination order (Definition 1, min-fill / natural /
+// given / DFS pseudo-tree post-order, Sections 2 and 6.2), buckets and
+// mini-bucket partitions (Algorithms 1-2), elimination-tree levels, the work
+// decomposition of each bucket for the UTIL kernel, the VALUE plan and the
+// arena layout.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <numeric>
+
+#include "gpube_internal.h"
+
+namespace gpube {
+
+static thread_local char g_err[512];
+
+int set_error(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+const char *last_error() { return g_err; }
+
+int cuda_error(cudaError_t e, const char *what)
+{
+    return set_error(GPUBE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ----------------------------------------------------------- orderings
+namespace {
+
+struct Bits {
+    int n = 0, words = 0;
+    std::vector<uint64_t> w;  // n rows of `words` 64-bit words
+    void init(int n_)
+    {
+        n = n_;
+        words = (n + 63) / 64;
+        w.assign(static_cast<size_t>(n) * words, 0);
+    }
+    uint64_t *row(int v) { return w.data() + static_cast<size_t>(v) * words; }
+    bool test(int v, int u) const { return (w[static_cast<size_t>(v) * words + u / 64] >> (u % 64)) & 1; }
+    void set(int v, int u) { row(v)[u / 64] |= 1ULL << (u % 64); }
+};
+
+}  // namespace
+
+// Greedy min-fill: eliminate the variable whose remaining neighbours have the
+// fewest unconnected pairs; ties: fewer remaining neighbours, then lower id.
+// Only the neighbourhood (distance <= 2) of an eliminated variable changes
+// its fill, so only that region is rescored.
+std::vector<int32_t> order_minfill(const wcsp &w, int32_t *width)
+{
+    const int n = w.n;
+    Bits adj;
+    adj.init(n);
+    for (int v = 0; v < n; ++v)
+        for (int u : w.adj[v]) adj.set(v, u);
+    std::vector<uint64_t> alive(adj.words, 0);
+    for (int v = 0; v < n; ++v) alive[v / 64] |= 1ULL << (v % 64);
+    std::vector<int64_t> fill(n, 0);
+    std::vector<int32_t> deg(n, 0);
+    std::vector<uint64_t> nbv(adj.words);
+    auto neighbours = [&](int v, std::vector<int> &out) {
+        out.clear();
+        const uint64_t *r = adj.row(v);
+        for (int k = 0; k < adj.words; ++k) {
+            uint64_t x = r[k] & alive[k];
+            while (x) {
+                int b = __builtin_ctzll(x);
+                out.push_back(k * 64 + b);
+                x &= x - 1;
+            }
+        }
+    };
+    std::vector<int> nb, nb2;
+    auto score = [&](int v) {
+        neighbours(v, nb2);
+        const uint64_t *r = adj.row(v);
+        int64_t missing = 0;
+        for (int a : nb2) {
+            const uint64_t *ra = adj.row(a);
+            int64_t c = 0;
+            for (int k = 0; k < adj.words; ++k) c += __builtin_popcountll(r[k] & alive[k] & ~ra[k]);
+            missing += c - 1;  // a itself is in N(v) but not in N(a)
+        }
+        fill[v] = missing / 2;
+        deg[v] = static_cast<int32_t>(nb2.size());
+    };
+    for (int v = 0; v < n; ++v) score(v);
+    std::vector<int32_t> order;
+    order.reserve(n);
+    std::vector<char> gone(n, 0), dirty(n, 0);
+    int32_t wmax = 0;
+    for (int t = 0; t < n; ++t) {
+        int best = -1;
+        for (int v = 0; v < n; ++v) {
+            if (gone[v]) continue;
+            if (best < 0 || fill[v] < fill[best] || (fill[v] == fill[best] && deg[v] < deg[best])) best = v;
+        }
+        neighbours(best, nb);
+        wmax = std::max<int32_t>(wmax, static_cast<int32_t>(nb.size()));
+        for (int a : nb)
+            for (int b : nb)
+                if (a != b) adj.set(a, b);
+        gone[best] = 1;
+        alive[best / 64] &= ~(1ULL << (best % 64));
+        order.push_back(best);
+        std::vector<int> touched;
+        for (int a : nb) {
+            if (!dirty[a]) {
+                dirty[a] = 1;
+                touched.push_back(a);
+            }
+            neighbours(a, nb2);
+            for (int u : nb2)
+                if (!dirty[u]) {
+                    dirty[u] = 1;
+                    touched.push_back(u);
+                }
+        }
+        for (int u : touched) {
+            score(u);
+            dirty[u] = 0;
+        }
+    }
+    if (width) *width = wmax;
+    return order;
+}
+
+// Induced width along an order (Definition 1).
+int32_t induced_width(const wcsp &w, const std::vector<int32_t> &order)
+{
+    const int n = w.n;
+    Bits adj;
+    adj.init(n);
+    for (int v = 0; v < n; ++v)
+        for (int u : w.adj[v]) adj.set(v, u);
+    std::vector<char> gone(n, 0);
+    int32_t wmax = 0;
+    std::vector<int> nb;
+    for (int v : order) {
+        nb.clear();
+        for (int u = 0; u < n; ++u)
+            if (!gone[u] && adj.test(v, u)) nb.push_back(u);
+        wmax = std::max<int32_t>(wmax, static_cast<int32_t>(nb.size()));
+        for (int a : nb)
+            for (int b : nb)
+                if (a != b) adj.set(a, b);
+        gone[v] = 1;
+    }
+    return wmax;
+}
+
+// Vertices by (degree descending, id ascending): the pseudo-tree priority of
+// Section 6.2.
+static std::vector<int32_t> degree_rank(const wcsp &w)
+{
+    std::vector<int32_t> r(w.n);
+    std::iota(r.begin(), r.end(), 0);
+    std::stable_sort(r.begin(), r.end(), [&](int a, int b) { return w.adj[a].size() > w.adj[b].size(); });
+    return r;
+}
+
+// DFS pseudo-tree (Definition 2): every non-tree edge of a DFS tree joins an
+// ancestor and a descendant.  Roots and children by degree_rank.
+std::vector<int32_t> dfs_pseudotree(const wcsp &w)
+{
+    const int n = w.n;
+    std::vector<int32_t> rank = degree_rank(w), where(n);
+    for (int i = 0; i < n; ++i) where[rank[i]] = i;
+    std::vector<std::vector<int32_t>> nbr(n);
+    for (int v = 0; v < n; ++v) {
+        nbr[v] = w.adj[v];
+        std::sort(nbr[v].begin(), nbr[v].end(), [&](int a, int b) { return where[a] < where[b]; });
+    }
+    std::vector<int32_t> parent(n, -1);
+    std::vector<char> seen(n, 0);
+    std::vector<std::pair<int, size_t>> st;
+    for (int r : rank) {
+        if (seen[r]) continue;
+        seen[r] = 1;
+        st.push_back({r, 0});
+        while (!st.empty()) {
+            auto &top = st.back();
+            if (top.second < nbr[top.first].size()) {
+                int u = nbr[top.first][top.second++];
+                if (!seen[u]) {
+                    seen[u] = 1;
+                    parent[u] = top.first;
+                    st.push_back({u, 0});
+                }
+            } else {
+                st.pop_back();
+            }
+        }
+    }
+    return parent;
+}
+
+// Post-order of a pseudo-tree (children and roots by degree_rank), after
+// checking that parent[] is a forest on which every constraint lies on one
+// root-to-leaf path.
+int pseudotree_order(const wcsp &w, const int32_t *parent, std::vector<int32_t> &order)
+{
+    const int n = w.n;
+    for (int v = 0; v < n; ++v)
+        if (parent[v] < -1 || parent[v] >= n || parent[v] == v)
+            return set_error(GPUBE_EINVAL, "parent[%d] = %d is not a variable", v, parent[v]);
+    std::vector<int32_t> rank = degree_rank(w), where(n);
+    for (int i = 0; i < n; ++i) where[rank[i]] = i;
+    std::vector<std::vector<int32_t>> kids(n);
+    std::vector<int32_t> roots;
+    for (int r : rank) {
+        if (parent[r] < 0) roots.push_back(r);
+        else kids[parent[r]].push_back(r);
+    }
+    order.clear();
+    std::vector<int32_t> tin(n, -1), tout(n, -1);
+    int clock = 0;
+    std::vector<std::pair<int, size_t>> st;
+    for (int r : roots) {
+        st.push_back({r, 0});
+        tin[r] = clock++;
+        while (!st.empty()) {
+            auto &top = st.back();
+            if (top.second < kids[top.first].size()) {
+                int c = kids[top.first][top.second++];
+                tin[c] = clock++;
+                st.push_back({c, 0});
+            } else {
+                tout[top.first] = clock++;
+                order.push_back(top.first);
+                st.pop_back();
+            }
+        }
+    }
+    if (static_cast<int>(order.size()) != n)
+        return set_error(GPUBE_EINVAL, "parent[] has a cycle (%zu of %d nodes reachable)", order.size(), n);
+    auto is_anc = [&](int a, int b) { return tin[a] <= tin[b] && tout[b] <= tout[a]; };
+    for (int j = 0; j < w.nf; ++j) {
+        const auto &s = w.scope[j];
+        for (size_t x = 0; x < s.size(); ++x)
+            for (size_t y = x + 1; y < s.size(); ++y)
+                if (!is_anc(s[x], s[y]) && !is_anc(s[y], s[x]))
+                    return set_error(GPUBE_EINVAL,
+                                     "constraint %d joins %d and %d on different branches of the pseudo-tree",
+                                     j, s[x], s[y]);
+    }
+    return GPUBE_OK;
+}
+
+// ------------------------------------------------------------- planning
+static bool mb_fits(const wcsp &w, int mode, int z, const std::vector<int32_t> &u)
+{
+    const int k = static_cast<int>(u.size());
+    if (mode == GPUBE_IB_SEP_VARS) return k - 1 <= z;
+    if (mode == GPUBE_IB_JOINT_VARS) return k <= z;
+    // product of the domains <= 2^z, exactly
+    if (z < 0) return false;
+    unsigned __int128 p = 1, lim = (z >= 120) ? ~static_cast<unsigned __int128>(0) : (static_cast<unsigned __int128>(1) << z);
+    for (int v : u) {
+        p *= static_cast<unsigned>(w.dom[v]);
+        if (p > lim) return false;
+    }
+    return true;
+}
+
+int build_plan(const wcsp &w, int kind, int i_bound, const int32_t *parent, const solve_opts &o, Plan &P)
+{
+    const int n = w.n;
+    P = Plan();
+    P.kind = kind;
+    P.i_bound = i_bound;
+    P.ibound_mode = o.ibound_mode;
+    if (kind == GPUBE_KIND_MBE && (o.ibound_mode < 0 || o.ibound_mode > 2))
+        return set_error(GPUBE_EINVAL, "unknown ibound_mode %d", o.ibound_mode);
+    if (o.lo_target > 0) P.lo_target = o.lo_target;
+    if (o.stage_max_entries > 0) P.stage_max_entries = o.stage_max_entries;
+    if (o.stage_max_entries < 0) P.stage_max_entries = 0;
+
+    // 1. elimination order
+    int okind = o.order_kind;
+    if (kind == GPUBE_KIND_DPOP) okind = GPUBE_ORDER_PSEUDOTREE;
+    const int32_t *tree = (kind == GPUBE_KIND_DPOP) ? parent : o.parent;
+    switch (okind) {
+    case GPUBE_ORDER_MINFILL: P.order = order_minfill(w, nullptr); break;
+    case GPUBE_ORDER_NATURAL:
+        P.order.resize(n);
+        std::iota(P.order.begin(), P.order.end(), 0);
+        break;
+    case GPUBE_ORDER_BEST: {
+        int32_t wm = 0;
+        P.order = order_minfill(w, &wm);
+        std::vector<int32_t> nat(n);
+        std::iota(nat.begin(), nat.end(), 0);
+        if (induced_width(w, nat) < wm) P.order = nat;
+        break;
+    }
+    case GPUBE_ORDER_GIVEN: {
+        if (!o.order) return set_error(GPUBE_EINVAL, "GPUBE_ORDER_GIVEN without an order");
+        P.order.assign(o.order, o.order + n);
+        std::vector<char> seen(n, 0);
+        for (int v : P.order) {
+            if (v < 0 || v >= n || seen[v]) return set_error(GPUBE_EINVAL, "order is not a permutation");
+            seen[v] = 1;
+        }
+        break;
+    }
+    case GPUBE_ORDER_PSEUDOTREE: {
+        std::vector<int32_t> pt;
+        if (!tree) {
+            pt = dfs_pseudotree(w);
+            tree = pt.data();
+        }
+        int rc = pseudotree_order(w, tree, P.order);
+        if (rc) return rc;
+        break;
+    }
+    default: return set_error(GPUBE_EINVAL, "unknown order kind %d", okind);
+    }
+    P.pos.assign(n, 0);
+    for (int t = 0; t < n; ++t) P.pos[P.order[t]] = t;
+
+    // 2. original functions in canonical scope order (descending position)
+    auto canonical = [&](std::vector<int32_t> s) {
+        std::sort(s.begin(), s.end(), [&](int a, int b) { return P.pos[a] > P.pos[b]; });
+        return s;
+    };
+    std::vector<std::vector<int32_t>> bucket(n);
+    P.funcs.resize(w.nf);
+    for (int j = 0; j < w.nf; ++j) {
+        Func &f = P.funcs[j];
+        f.scope = canonical(w.scope[j]);
+        f.size = 1;
+        for (int v : f.scope) f.size *= w.dom[v];
+        if (f.scope.empty()) {
+            P.const_sum += (w.cost_type == WCSP_FP32_LOG) ? static_cast<double>(w.ftab[j][0])
+                                                          : static_cast<double>(w.itab[j][0]);
+        } else {
+            bucket[f.scope.back()].push_back(j);
+        }
+    }
+
+    // 3. Algorithm 1 / 2: buckets, partitions, bucket functions
+    const bool mbe = (kind == GPUBE_KIND_MBE);
+    for (int t = 0; t < n; ++t) {
+        const int v = P.order[t];
+        std::vector<int32_t> B = bucket[v];
+        if (B.empty()) continue;
+        std::stable_sort(B.begin(), B.end(), [&](int a, int b) {
+            if (P.funcs[a].scope.size() != P.funcs[b].scope.size())
+                return P.funcs[a].scope.size() > P.funcs[b].scope.size();
+            return a < b;
+        });
+        std::vector<std::vector<int32_t>> mb_funcs, mb_vars;  // vars kept sorted by id
+        for (int fid : B) {
+            std::vector<int32_t> fv = P.funcs[fid].scope;
+            std::sort(fv.begin(), fv.end());
+            int placed = -1;
+            if (mbe) {
+                for (size_t b = 0; b < mb_vars.size() && placed < 0; ++b) {
+                    std::vector<int32_t> u;
+                    std::set_union(mb_vars[b].begin(), mb_vars[b].end(), fv.begin(), fv.end(),
+                                   std::back_inserter(u));
+                    if (mb_fits(w, o.ibound_mode, i_bound, u)) {
+                        mb_vars[b] = u;
+                        placed = static_cast<int>(b);
+                    }
+                }
+            } else if (!mb_vars.empty()) {
+                std::vector<int32_t> u;
+                std::set_union(mb_vars[0].begin(), mb_vars[0].end(), fv.begin(), fv.end(), std::back_inserter(u));
+                mb_vars[0] = u;
+                placed = 0;
+            }
+            if (placed < 0) {
+                mb_vars.push_back(fv);
+                mb_funcs.emplace_back();
+                placed = static_cast<int>(mb_vars.size()) - 1;
+            }
+            mb_funcs[placed].push_back(fid);
+        }
+        for (size_t b = 0; b < mb_vars.size(); ++b) {
+            Task T;
+            T.var = v;
+            T.d = w.dom[v];
+            std::vector<int32_t> sep;
+            for (int u : mb_vars[b])
+                if (u != v) sep.push_back(u);
+            T.sep = canonical(sep);
+            T.inputs = mb_funcs[b];
+            T.rows = 1;
+            for (int u : T.sep) {
+                T.rows *= w.dom[u];
+                if (T.rows > INT32_MAX)
+                    return set_error(GPUBE_ENOMEM, "bucket of variable %d needs a table of more than 2^31 entries", v);
+            }
+            int lev = 0;
+            for (int fid : T.inputs)
+                if (P.funcs[fid].task >= 0) lev = std::max(lev, P.tasks[P.funcs[fid].task].level + 1);
+            T.level = lev;
+            const int tid = static_cast<int>(P.tasks.size());
+            P.width = std::max<int32_t>(P.width, static_cast<int32_t>(T.sep.size()));
+            P.max_inputs = std::max<int32_t>(P.max_inputs, static_cast<int32_t>(T.inputs.size()));
+            P.util_entries += T.rows * T.d;
+            P.out_entries += T.rows;
+            for (int fid : T.inputs) P.in_entries += P.funcs[fid].size;
+            Func out;
+            out.scope = T.sep;
+            out.size = T.rows;
+            out.task = tid;
+            P.tasks.push_back(std::move(T));
+            P.funcs.push_back(std::move(out));
+            if (!P.tasks.back().sep.empty()) bucket[P.tasks.back().sep.back()].push_back(w.nf + tid);
+        }
+    }
+
+    // 4. elimination-tree levels
+    P.n_levels = 0;
+    for (const Task &T : P.tasks) P.n_levels = std::max(P.n_levels, T.level + 1);
+    P.level_order.resize(P.tasks.size());
+    std::iota(P.level_order.begin(), P.level_order.end(), 0);
+    std::stable_sort(P.level_order.begin(), P.level_order.end(),
+                     [&](int a, int b) { return P.tasks[a].level < P.tasks[b].level; });
+    P.level_off.assign(P.n_levels + 1, 0);
+    for (const Task &T : P.tasks) P.level_off[T.level + 1]++;
+    for (int l = 0; l < P.n_levels; ++l) P.level_off[l + 1] += P.level_off[l];
+    return GPUBE_OK;
+}
+
+// ------------------------------------------------- work decomposition
+// Stride of each separator digit in each input's canonical layout (0 when
+// the input does not mention it), plus the output's own strides (slot F).
+void task_strides(const wcsp &w, const Plan &P, const Task &T, std::vector<int32_t> &st)
+{
+    const int m = static_cast<int>(T.sep.size());
+    const int F = static_cast<int>(T.inputs.size());
+    st.assign(static_cast<size_t>(F + 1) * m, 0);
+    for (int f = 0; f < F; ++f) {
+        const Func &fn = P.funcs[T.inputs[f]];
+        int64_t s = 1;
+        for (int k = static_cast<int>(fn.scope.size()) - 1; k >= 0; --k) {
+            const int u = fn.scope[k];
+            for (int j = 0; j < m; ++j)
+                if (T.sep[j] == u) st[static_cast<size_t>(f) * m + j] = static_cast<int32_t>(s);
+            s *= w.dom[u];
+        }
+    }
+    int64_t s = 1;
+    for (int j = m - 1; j >= 0; --j) {
+        st[static_cast<size_t>(F) * m + j] = static_cast<int32_t>(s);
+        s *= w.dom[T.sep[j]];
+    }
+}
+
+// Split every task's rows into (hi, lo), choose the hi iteration order and
+// the staged inputs.
+void shape_tasks(const wcsp &w, Plan &P)
+{
+    for (Task &T : P.tasks) {
+        const int m = static_cast<int>(T.sep.size());
+        const int F = static_cast<int>(T.inputs.size());
+        T.L = 0;
+        T.P_lo = 1;
+        for (int j = m - 1; j >= 0 && T.P_lo < P.lo_target; --j) {
+            T.P_lo *= w.dom[T.sep[j]];
+            T.L++;
+        }
+        T.H = T.rows / T.P_lo;
+        // hi digits absent from the largest input iterate fastest: a thread's
+        // consecutive rows then reread the same input entries
+        int big = 0;
+        for (int f = 1; f < F; ++f)
+            if (P.funcs[T.inputs[f]].size > P.funcs[T.inputs[big]].size) big = f;
+        const auto &bs = P.funcs[T.inputs[big]].scope;
+        std::vector<int32_t> absent, present;
+        for (int j = m - T.L - 1; j >= 0; --j) {
+            bool in = std::find(bs.begin(), bs.end(), T.sep[j]) != bs.end();
+            (in ? present : absent).push_back(j);
+        }
+        T.hperm = absent;
+        T.hperm.insert(T.hperm.end(), present.begin(), present.end());
+        T.sa = static_cast<int32_t>(align_up(F + 1, 4));
+        T.sb = static_cast<int32_t>(align_up(std::max(F, 1), 4));
+        // stage the smallest inputs while they fit
+        T.stage_off.assign(F, -1);
+        T.stage_bytes = 0;
+        std::vector<int> idx(F);
+        std::iota(idx.begin(), idx.end(), 0);
+        std::stable_sort(idx.begin(), idx.end(),
+                         [&](int a, int b) { return P.funcs[T.inputs[a]].size < P.funcs[T.inputs[b]].size; });
+        for (int f : idx) {
+            const Func &fn = P.funcs[T.inputs[f]];
+            const int64_t sz = fn.size;
+            if (sz > P.stage_max_entries) break;
+            if (fn.ext && (sz * 4) % kStageAlign) continue;  // a copy would read past the caller's table
+            const int64_t bytes = static_cast<int64_t>(align_up(sz * 4, kStageAlign));
+            if (T.stage_bytes + bytes > P.stage_max_bytes) break;
+            T.stage_off[f] = T.stage_bytes;
+            T.stage_bytes += static_cast<int32_t>(bytes);
+        }
+    }
+}
+
+}  // namespace gpube

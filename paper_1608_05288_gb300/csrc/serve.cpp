@@ -1,0 +1,417 @@
+// Continuous-batching server for streams of WCSP / DCOP instances.
+//
+// Admission: a request is planned on submit (no GPU work); its device need
+// (the plan's arena size, from the separator sizes, i.e. the induced width)
+// is known before anything is allocated.  Requests are admitted in arrival
+// order while a slot is free and a first-fit allocator finds room for them in
+// the server's memory budget; their tables stay resident until they finish.
+//
+// Batching: each server step merges, for every admitted request, the tasks
+// of its next elimination-tree level into ONE persistent UTIL launch (the
+// same kernel and device work queue as a single instance's batched level).
+// A request admitted while others are running joins the next launch, so the
+// work of requests of different sizes overlaps on the device.  A request
+// whose last level has run gets its VALUE kernel and an asynchronous copy of
+// its result; it is retired (memory returned) once that copy has landed.
+#include <string.h>
+
+#include <algorithm>
+#include <deque>
+#include <map>
+#include <vector>
+
+#include "gpube_internal.h"
+
+using namespace gpube;
+
+namespace {
+
+#define SRV_TRY(call)                                           \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_error(e_, #call);    \
+    } while (0)
+
+size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// First-fit allocator over [0, size) with coalescing on free.
+struct FirstFit {
+    std::map<size_t, size_t> free_blocks;  // offset -> bytes
+    size_t used = 0, peak = 0;
+    void init(size_t size)
+    {
+        free_blocks.clear();
+        if (size) free_blocks[0] = size;
+        used = peak = 0;
+    }
+    bool alloc(size_t bytes, size_t *off)
+    {
+        bytes = al(bytes, 256);
+        for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, at = it->first + bytes;
+                free_blocks.erase(it);
+                if (rest) free_blocks[at] = rest;
+                used += bytes;
+                peak = std::max(peak, used);
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes)
+    {
+        bytes = al(bytes, 256);
+        used -= bytes;
+        auto it = free_blocks.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_blocks.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_blocks.erase(nx);
+        }
+        if (it != free_blocks.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_blocks.erase(it);
+            }
+        }
+    }
+};
+
+enum { kQueued = 0, kActive = 1, kValue = 2, kDone = 3, kFailed = 4 };
+
+struct Request {
+    int64_t id = 0;
+    util_state *st = nullptr;
+    size_t off = 0, bytes = 0;
+    int slot = -1, next_level = 0, state = kQueued, rc = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    cudaEvent_t up_ev = nullptr, done_ev = nullptr;
+    bool up_waited = false;
+    std::vector<int32_t> sigma;
+    solve_result res{};
+};
+
+}  // namespace
+
+struct gpube_server {
+    size_t budget = 0;
+    int max_slots = 1;
+    unsigned char *base = nullptr;
+    bool owns = false;
+    cudaStream_t stream = nullptr, up_stream = nullptr;
+    FirstFit alloc;
+    std::deque<Request *> queue;
+    std::map<int64_t, Request *> reqs;
+    std::vector<Request *> active;
+    std::vector<int> free_slots;
+    std::vector<unsigned char *> pinned;   // per slot: status, result, assignment
+    std::vector<size_t> pinned_cap;
+    int64_t next_id = 0;
+    // merged launch descriptors (double buffered)
+    unsigned char *dbuf[2] = {nullptr, nullptr};
+    size_t dcap[2] = {0, 0};
+    cudaEvent_t dev_ev[2] = {nullptr, nullptr};
+    bool dev_used[2] = {false, false};
+    int flip = 0;
+    int32_t *work = nullptr;  // [0..1] counters, [2] status
+    int num_sms = 0, threads = 256;
+    int64_t launches = 0, max_inflight = 0;
+    double t0 = 0;
+};
+
+extern "C" int srv_create(size_t budget_bytes, int32_t max_slots, void *arena, size_t arena_bytes, void *stream,
+                          gpube_server **out)
+{
+    if (!out || budget_bytes == 0 || max_slots < 1) return set_error(GPUBE_EINVAL, "bad server arguments");
+    *out = nullptr;
+    int dev = 0;
+    SRV_TRY(cudaGetDevice(&dev));
+    gpube_server *s = new gpube_server();
+    s->budget = budget_bytes;
+    s->max_slots = max_slots;
+    s->stream = static_cast<cudaStream_t>(stream);
+    cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (arena) {
+        if (arena_bytes < budget_bytes || reinterpret_cast<uintptr_t>(arena) % 256) {
+            delete s;
+            return set_error(GPUBE_EINVAL, "arena smaller than the budget or not 256-byte aligned");
+        }
+        s->base = static_cast<unsigned char *>(arena);
+    } else {
+        void *p = nullptr;
+        if (cudaMalloc(&p, budget_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return set_error(GPUBE_ENOMEM, "cudaMalloc of the %zu-byte budget failed", budget_bytes);
+        }
+        s->base = static_cast<unsigned char *>(p);
+        s->owns = true;
+    }
+    s->alloc.init(budget_bytes);
+    for (int i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->pinned.assign(max_slots, nullptr);
+    s->pinned_cap.assign(max_slots, 0);
+    cudaError_t e = cudaStreamCreateWithFlags(&s->up_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&s->work), 64);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaEventCreateWithFlags(&s->dev_ev[b], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->work, 0, 64, s->stream);
+    if (e != cudaSuccess) {
+        int rc = cuda_error(e, "srv_create");
+        srv_free(s);
+        return rc;
+    }
+    s->t0 = now_ms();
+    *out = s;
+    return GPUBE_OK;
+}
+
+extern "C" int64_t srv_submit(gpube_server *s, wcsp *w, int32_t kind, int32_t i_bound, const int32_t *parent,
+                              const solve_opts *opts)
+{
+    if (!s || !w) return set_error(GPUBE_EINVAL, "null argument");
+    solve_opts o;
+    if (opts) o = *opts;
+    else solve_opts_init(&o);
+    o.block_threads = s->threads;  // one CTA size for every merged launch
+    o.batched = 1;
+    o.use_graph = 0;
+    util_state *st = nullptr;
+    int rc = util_plan(w, kind, i_bound, parent, &o, &st);
+    if (rc) return rc;
+    if (al(st->arena_bytes, 256) > s->budget) {
+        util_state_free(st);
+        return set_error(GPUBE_ENOMEM, "request needs %zu bytes, the budget is %zu", st->arena_bytes, s->budget);
+    }
+    Request *r = new Request();
+    r->id = s->next_id++;
+    r->st = st;
+    r->bytes = st->arena_bytes;
+    r->t_submit = now_ms() - s->t0;
+    s->reqs[r->id] = r;
+    s->queue.push_back(r);
+    return r->id;
+}
+
+static int admit(gpube_server *s)
+{
+    while (!s->queue.empty() && !s->free_slots.empty()) {
+        Request *r = s->queue.front();
+        size_t off;
+        if (!s->alloc.alloc(r->bytes, &off)) break;  // wait until memory frees up
+        s->queue.pop_front();
+        r->off = off;
+        r->slot = s->free_slots.back();
+        s->free_slots.pop_back();
+        const size_t need = 24 + 4 * static_cast<size_t>(std::max(r->st->w->n, 1));
+        if (s->pinned_cap[r->slot] < need) {
+            if (s->pinned[r->slot]) cudaFreeHost(s->pinned[r->slot]);
+            s->pinned[r->slot] = nullptr;
+            SRV_TRY(cudaMallocHost(reinterpret_cast<void **>(&s->pinned[r->slot]), need));
+            s->pinned_cap[r->slot] = need;
+        }
+        // uploads go to a side stream so that admission does not wait for the
+        // launches in flight; the compute stream waits on them by event
+        int rc = util_bind(r->st, s->base + off, r->bytes, s->up_stream);
+        if (rc) return rc;
+        SRV_TRY(cudaEventCreateWithFlags(&r->up_ev, cudaEventDisableTiming));
+        SRV_TRY(cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming));
+        SRV_TRY(cudaEventRecord(r->up_ev, s->up_stream));
+        r->st->stream = s->stream;  // everything after the upload runs on the compute stream
+        r->state = kActive;
+        r->next_level = 0;
+        r->t_admit = now_ms() - s->t0;
+        s->active.push_back(r);
+    }
+    s->max_inflight = std::max<int64_t>(s->max_inflight, static_cast<int64_t>(s->active.size()));
+    return GPUBE_OK;
+}
+
+static int retire(gpube_server *s)
+{
+    for (size_t i = 0; i < s->active.size();) {
+        Request *r = s->active[i];
+        if (r->state == kValue && cudaEventQuery(r->done_ev) == cudaSuccess) {
+            const unsigned char *pb = s->pinned[r->slot];
+            int32_t status;
+            memcpy(&status, pb, 4);
+            double rr[2];
+            memcpy(rr, pb + 8, 16);
+            const int n = r->st->w->n;
+            r->sigma.assign(reinterpret_cast<const int32_t *>(pb + 24), reinterpret_cast<const int32_t *>(pb + 24) + n);
+            r->res.bound = rr[0];
+            r->res.cost = rr[1];
+            const Plan &P = r->st->plan;
+            r->res.induced_width = P.width;
+            r->res.n_tasks = static_cast<int32_t>(P.tasks.size());
+            r->res.n_levels = P.n_levels;
+            r->res.util_entries = P.util_entries;
+            r->res.alg_bytes = 4 * P.in_entries + 5 * P.out_entries;
+            r->res.plan_ms = r->st->plan_ms;
+            r->rc = status ? GPUBE_ETIMEDOUT : GPUBE_OK;
+            r->state = status ? kFailed : kDone;
+            r->t_done = now_ms() - s->t0;
+            s->alloc.release(r->off, r->bytes);
+            s->free_slots.push_back(r->slot);
+            cudaEventDestroy(r->up_ev);
+            cudaEventDestroy(r->done_ev);
+            r->up_ev = r->done_ev = nullptr;
+            r->st->sync_on_free = false;  // its work is complete (done_ev)
+            util_state_free(r->st);
+            r->st = nullptr;
+            s->active.erase(s->active.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+    return GPUBE_OK;
+}
+
+extern "C" int srv_step(gpube_server *s)
+{
+    if (!s) return set_error(GPUBE_EINVAL, "null server");
+    int rc = retire(s);
+    if (!rc) rc = admit(s);
+    if (rc) return rc;
+    // merge the next level of every running request into one launch
+    std::vector<TaskDev> tds;
+    std::vector<Request *> finishing;
+    int smem = 0;
+    for (Request *r : s->active) {
+        if (r->state != kActive) continue;
+        if (!r->up_waited) {
+            SRV_TRY(cudaStreamWaitEvent(s->stream, r->up_ev, 0));
+            r->up_waited = true;
+        }
+        const Plan &P = r->st->plan;
+        if (r->next_level < P.n_levels) {
+            const TaskDev *td = reinterpret_cast<const TaskDev *>(
+                r->st->host_blob.data() + (r->st->dl.taskdev - r->st->desc_off));
+            for (int i = P.level_off[r->next_level]; i < P.level_off[r->next_level + 1]; ++i) {
+                tds.push_back(td[i]);
+                smem = std::max(smem, td[i].stage_bytes);
+            }
+            r->next_level++;
+        }
+        if (r->next_level >= P.n_levels) finishing.push_back(r);
+    }
+    if (!tds.empty()) {
+        const int b = s->flip;
+        s->flip ^= 1;
+        if (s->dev_used[b]) SRV_TRY(cudaEventSynchronize(s->dev_ev[b]));
+        const size_t nt = tds.size();
+        const size_t bytes = al(sizeof(TaskDev) * nt, 16) + 4 * (nt + 1);
+        if (s->dcap[b] < bytes) {
+            if (s->dbuf[b]) cudaFree(s->dbuf[b]);
+            s->dbuf[b] = nullptr;
+            const size_t cap = std::max<size_t>(bytes * 2, 1 << 16);
+            SRV_TRY(cudaMalloc(reinterpret_cast<void **>(&s->dbuf[b]), cap));
+            s->dcap[b] = cap;
+        }
+        std::vector<unsigned char> host(bytes);
+        memcpy(host.data(), tds.data(), sizeof(TaskDev) * nt);
+        int32_t *pre = reinterpret_cast<int32_t *>(host.data() + al(sizeof(TaskDev) * nt, 16));
+        int64_t tot = 0;
+        for (size_t i = 0; i < nt; ++i) {
+            pre[i] = static_cast<int32_t>(tot);
+            tot += tds[i].n_items;
+        }
+        pre[nt] = static_cast<int32_t>(tot);
+        if (tot > INT32_MAX / 2) return set_error(GPUBE_ENOMEM, "merged launch has too many work items");
+        SRV_TRY(cudaMemcpyAsync(s->dbuf[b], host.data(), bytes, cudaMemcpyHostToDevice, s->stream));
+        LaunchDev L{};
+        L.tasks = reinterpret_cast<const TaskDev *>(s->dbuf[b]);
+        L.prefix = reinterpret_cast<const int32_t *>(s->dbuf[b] + al(sizeof(TaskDev) * nt, 16));
+        L.n_tasks = static_cast<int32_t>(nt);
+        L.total_items = static_cast<int32_t>(tot);
+        L.counter = s->work + b;
+        L.status = s->work + 2;
+        L.top_k = s->active.front()->st->w->top_k;
+        SRV_TRY(cudaMemsetAsync(L.counter, 0, 4, s->stream));
+        const int cost_type = s->active.front()->st->w->cost_type;
+        const int64_t cap = static_cast<int64_t>(util_max_blocks_per_sm(cost_type, s->threads, smem)) * s->num_sms;
+        const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(tot, cap)));
+        SRV_TRY(launch_util(L, cost_type, grid, s->threads, smem, s->stream));
+        SRV_TRY(cudaEventRecord(s->dev_ev[b], s->stream));
+        s->dev_used[b] = true;
+        s->launches++;
+    }
+    for (Request *r : finishing) {
+        util_state *st = r->st;
+        st->ran = true;
+        SRV_TRY(launch_value(st->vdev, st->w->cost_type, st->value_smem, s->stream));
+        const size_t need = 24 + 4 * static_cast<size_t>(std::max(st->w->n, 1));
+        SRV_TRY(cudaMemcpyAsync(s->pinned[r->slot], st->base + st->status_off, need, cudaMemcpyDeviceToHost,
+                                s->stream));
+        SRV_TRY(cudaEventRecord(r->done_ev, s->stream));
+        r->state = kValue;
+    }
+    return static_cast<int>(s->queue.size() + s->active.size());
+}
+
+extern "C" int srv_result(gpube_server *s, int64_t id, int32_t *assignment, solve_result *res)
+{
+    if (!s) return set_error(GPUBE_EINVAL, "null server");
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return set_error(GPUBE_EINVAL, "unknown request %lld", static_cast<long long>(id));
+    Request *r = it->second;
+    if (r->state == kFailed) return set_error(r->rc, "request %lld failed", static_cast<long long>(id));
+    if (r->state != kDone) return GPUBE_EAGAIN;
+    if (assignment) std::copy(r->sigma.begin(), r->sigma.end(), assignment);
+    if (res) {
+        int32_t *keep = res->assignment;
+        *res = r->res;
+        res->assignment = keep;
+        if (keep && keep != assignment) std::copy(r->sigma.begin(), r->sigma.end(), keep);
+    }
+    return GPUBE_OK;
+}
+
+extern "C" int srv_times(gpube_server *s, int64_t id, double *t_submit, double *t_admit, double *t_done)
+{
+    if (!s) return set_error(GPUBE_EINVAL, "null server");
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return set_error(GPUBE_EINVAL, "unknown request");
+    Request *r = it->second;
+    if (t_submit) *t_submit = r->t_submit * 1e-3;
+    if (t_admit) *t_admit = r->t_admit * 1e-3;
+    if (t_done) *t_done = r->t_done * 1e-3;
+    return r->state == kDone ? GPUBE_OK : GPUBE_EAGAIN;
+}
+
+extern "C" int srv_stats(gpube_server *s, int64_t *launches, int64_t *peak_bytes, int64_t *max_inflight)
+{
+    if (!s) return set_error(GPUBE_EINVAL, "null server");
+    if (launches) *launches = s->launches;
+    if (peak_bytes) *peak_bytes = static_cast<int64_t>(s->alloc.peak);
+    if (max_inflight) *max_inflight = s->max_inflight;
+    return GPUBE_OK;
+}
+
+extern "C" void srv_free(gpube_server *s)
+{
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    if (s->up_stream) {
+        cudaStreamSynchronize(s->up_stream);
+        cudaStreamDestroy(s->up_stream);
+    }
+    for (auto &kv : s->reqs) {
+        Request *r = kv.second;
+        if (r->up_ev) cudaEventDestroy(r->up_ev);
+        if (r->done_ev) cudaEventDestroy(r->done_ev);
+        if (r->st) util_state_free(r->st);
+        delete r;
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (s->dbuf[b]) cudaFree(s->dbuf[b]);
+        if (s->dev_ev[b]) cudaEventDestroy(s->dev_ev[b]);
+    }
+    for (auto p : s->pinned)
+        if (p) cudaFreeHost(p);
+    if (s->work) cudaFree(s->work);
+    if (s->owns && s->base) cudaFree(s->base);
+    delete s;
+}

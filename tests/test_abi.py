@@ -1,0 +1,163 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+declared entry point, validates problems, and plans exactly what the oracle
+computes (orders, buckets, mini-bucket partitions, separators)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+import paper_1608_05288_gb300 as gb
+from paper_1608_05288_gb300 import _abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1608_05288_gb300 import _build
+    _build.build()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                                 src, flags=re.M):
+                names.add(m.group(1))
+    return names
+
+
+def test_exports_every_declared_symbol():
+    lib = C.CDLL(_abi.LIB_PATH)
+    names = _declared()
+    assert {"wcsp_load", "be_solve", "mbe_solve", "dpop_util", "value_propagate"} <= names
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(_abi.SIGNATURES) >= names
+
+
+def test_load_rejects_malformed():
+    inst = synth.paper_example()
+    gb.WCSP(inst)  # fine
+    bad = synth.paper_example()
+    bad.scopes[0] = np.array([0, 0], dtype=np.int32)  # repeated variable
+    with pytest.raises(gb.GpubeError) as e:
+        gb.WCSP(bad)
+    assert e.value.code == gb.EINVAL
+    bad = synth.paper_example()
+    bad.tables[1] = bad.tables[1][:3]  # wrong length
+    with pytest.raises(gb.GpubeError):
+        gb.WCSP(bad)
+    bad = synth.paper_example()
+    bad.tables[2] = bad.tables[2].copy()
+    bad.tables[2][0] = -1  # negative cost
+    with pytest.raises(gb.GpubeError):
+        gb.WCSP(bad)
+    bad = synth.paper_example()
+    bad.dom = np.array([2, 2, 0, 2], dtype=np.int32)
+    with pytest.raises(gb.GpubeError):
+        gb.WCSP(bad)
+
+
+def _lib_structure(st):
+    return [{"var": int(t["var"]), "sep": [int(x) for x in t["sep"]],
+             "inputs": sorted(int(x) for x in t["inputs"])} for t in st.tasks()]
+
+
+def _orc_structure(run):
+    return [{"var": int(t.var), "sep": [int(x) for x in t.sep],
+             "inputs": sorted(int(x) for x in t.inputs)} for t in run.tasks]
+
+
+def test_paper_example_plan(orc):
+    inst = synth.paper_example()
+    order = [3, 2, 1, 0]
+    be = gb.UtilState(inst, "be", order="given", order_array=order)
+    run = orc.eliminate(inst, np.array(order), "be")
+    assert _lib_structure(be) == _orc_structure(run)
+    assert be.info()["induced_width"] == 3
+    mbe = gb.UtilState(inst, "mbe", 1, order="given", order_array=order, ibound_mode="sep")
+    assert _lib_structure(mbe) == _orc_structure(orc.eliminate(inst, np.array(order), "sep", 1))
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_minfill_order_matches_oracle(orc, seed):
+    inst = synth.random_small(seed, n=12, dmax=3, n_funcs=16, max_arity=3)
+    st = gb.UtilState(inst, "be", order="minfill")
+    o, w = orc.minfill(inst)
+    assert list(st.order()) == list(o)
+    assert st.info()["induced_width"] == orc.eliminate(inst, o, "be", tables=False).width
+
+
+def test_config_orders_match_oracle(orc):
+    for idx in (0, 1, 2, 3):
+        inst = synth.config_instance(idx, 0)
+        st = gb.UtilState(inst, "be" if idx < 2 else "mbe", 16, order="best" if idx == 1 else "minfill",
+                          ibound_mode="log2")
+        o, _ = orc.best_order(inst) if idx == 1 else orc.minfill(inst)
+        assert list(st.order()) == list(o), idx
+
+
+@pytest.mark.parametrize("mode", ["sep", "joint", "log2"])
+@pytest.mark.parametrize("seed", range(6))
+def test_mbe_partition_matches_oracle(orc, seed, mode):
+    inst = synth.random_small(seed + 50, n=10, dmax=4, n_funcs=14, max_arity=3)
+    o, _ = orc.minfill(inst)
+    for z in (1, 2, 3, 4, 6):
+        st = gb.UtilState(inst, "mbe", z, order="given", order_array=o, ibound_mode=mode)
+        assert _lib_structure(st) == _orc_structure(orc.eliminate(inst, o, mode, z, tables=False))
+
+
+def test_config2_partition_matches_oracle(orc):
+    inst = synth.config_instance(2, 0)
+    o, _ = orc.minfill(inst)
+    st = gb.UtilState(inst, "mbe", 16, order="given", order_array=o, ibound_mode="log2")
+    run = orc.eliminate(inst, o, "log2", 16, tables=False)
+    assert _lib_structure(st) == _orc_structure(run)
+    info = st.info()
+    assert info["n_tasks"] == len(run.tasks)
+    assert info["util_entries"] == sum(int(t.rows) * int(inst.dom[t.var]) for t in run.tasks)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_dpop_plan_matches_oracle(orc, seed):
+    inst = synth.dcop_random(seed, n_range=(15, 30), d_range=(2, 4))
+    for parent in (None, inst.parent):
+        st = gb.UtilState(inst, "dpop", parent=parent)
+        par = orc.dfs_pseudotree(inst) if parent is None else parent
+        o = orc.pseudotree_order(inst, par)
+        assert list(st.order()) == list(o)
+        assert _lib_structure(st) == _orc_structure(orc.eliminate(inst, o, "be", tables=False))
+
+
+def test_dpop_rejects_invalid_pseudotree():
+    inst = synth.paper_example()
+    # a chain 0-1-2 with 3 hanging from 0: f(x2,x4) = (1,3) spans two branches
+    parent = np.array([-1, 0, 1, 0], dtype=np.int32)
+    with pytest.raises(gb.GpubeError) as e:
+        gb.UtilState(inst, "dpop", parent=parent)
+    assert e.value.code == gb.EINVAL
+    cyc = np.array([1, 2, 0, -1], dtype=np.int32)
+    with pytest.raises(gb.GpubeError):
+        gb.UtilState(inst, "dpop", parent=cyc)
+
+
+def test_plan_sizes_and_levels():
+    inst = synth.config_instance(1, 0)
+    st = gb.UtilState(inst, "be", order="best")
+    info = st.info()
+    assert info["induced_width"] == 12
+    assert info["n_tasks"] == 144
+    tasks = st.tasks()
+    assert max(t["rows"] for t in tasks) == 4 ** 12
+    # row-major elimination of a grid is a chain: one bucket per level
+    assert info["n_levels"] == 144
+    assert info["util_entries"] == sum(t["rows"] * 4 for t in tasks)
+    assert info["alg_bytes"] == 4 * info["in_entries"] + 5 * info["out_entries"]
+    assert info["arena_bytes"] >= 5 * info["out_entries"]

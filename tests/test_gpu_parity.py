@@ -1,0 +1,280 @@
+"""CUDA path vs the CPU oracle, through the C ABI (needs a GPU).
+
+Integer WCSPs: every bucket function, argmin table, the bound, the
+assignment and its cost are compared bit for bit (Theorem 1: the GPU tables
+are the sequential algorithm's tables).  Real (-log p) problems: within
+|delta| <= 1e-4 (1 + |value|), the assignment re-evaluated in fp64 by the
+oracle within the same bound.
+"""
+import numpy as np
+import pytest
+
+import synth
+import paper_1608_05288_gb300 as gb
+from gpu_util import check_tables, fp_close, run_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1608_05288_gb300 import _build
+    _build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+LAUNCH_SHAPES = [
+    dict(),                                                # defaults, batched
+    dict(batched=False),                                   # one launch per bucket
+    dict(use_graph=True),                                  # CUDA graph of the level sequence
+    dict(block_threads=32, rows_per_item=1, lo_target=8),  # many tiny items, ragged tails
+    dict(block_threads=64, rows_per_item=3, lo_target=5, stage_max_entries=-1),
+    dict(block_threads=512, rows_per_item=64, stage_max_entries=4),
+]
+
+
+def test_paper_example(orc):
+    inst = synth.paper_example()
+    order = np.array([3, 2, 1, 0])
+    for kind, mode, z in (("be", "be", 0), ("mbe", "sep", 1)):
+        st, res = run_state(inst, kind, z, order="given", order_array=order, ibound_mode="sep")
+        run = orc.eliminate(inst, order, mode, z)
+        check_tables(inst, st, run)
+        assert res.bound == run.bound and res.cost == run.cost
+        assert list(res.assignment) == list(run.sigma)
+
+
+@pytest.mark.parametrize("shape", range(len(LAUNCH_SHAPES)))
+@pytest.mark.parametrize("seed", range(6))
+def test_random_be_all_launch_shapes(orc, seed, shape):
+    inst = synth.random_small(seed, n=9, dmax=6, n_funcs=14, max_arity=4)
+    o, _ = orc.minfill(inst)
+    run = orc.eliminate(inst, o, "be")
+    st, res = run_state(inst, "be", order="given", order_array=o, **LAUNCH_SHAPES[shape])
+    check_tables(inst, st, run)
+    assert res.bound == run.bound == orc.bruteforce(inst)[0]
+    assert res.cost == run.cost and list(res.assignment) == list(run.sigma)
+
+
+@pytest.mark.parametrize("dom", [(1, 3), (2, 2), (3, 3), (5, 5), (7, 8), (9, 12), (2, 8)])
+def test_domain_classes(orc, dom):
+    # every templated domain size (2..8), the generic loop (1, 9..12)
+    inst = synth.random_small(17 + dom[0], n=7, dmin=dom[0], dmax=dom[1], n_funcs=10, max_arity=3)
+    o, _ = orc.minfill(inst)
+    run = orc.eliminate(inst, o, "be")
+    st, res = run_state(inst, "be", order="given", order_array=o, block_threads=64, lo_target=16)
+    check_tables(inst, st, run)
+    assert res.bound == run.bound and list(res.assignment) == list(run.sigma)
+
+
+@pytest.mark.parametrize("nf", [5, 9, 20])
+def test_many_inputs(orc, nf):
+    # buckets of more than 4 and more than 8 functions (register / generic paths)
+    rng = np.random.default_rng(nf)
+    n = 6
+    dom = np.array([3, 4, 2, 4, 3, 4], dtype=np.int32)
+    scopes, tables = [], []
+    for j in range(nf):
+        s = np.array(sorted(rng.choice(n, size=2, replace=False)), dtype=np.int32)
+        scopes.append(s)
+        tables.append(rng.integers(0, 30, size=int(dom[s[0]] * dom[s[1]])))
+    inst = synth.Instance("many", dom, scopes, tables, "int", 1 << 30)
+    o = np.arange(n)
+    run = orc.eliminate(inst, o, "be")
+    st, res = run_state(inst, "be", order="given", order_array=o)
+    check_tables(inst, st, run)
+    assert res.bound == run.bound
+
+
+@pytest.mark.parametrize("mode", ["sep", "joint", "log2"])
+def test_random_mbe(orc, mode):
+    for seed in range(4):
+        inst = synth.random_small(seed + 300, n=11, dmax=4, n_funcs=18, max_arity=3)
+        o, _ = orc.minfill(inst)
+        for z in (1, 2, 4):
+            run = orc.eliminate(inst, o, mode, z)
+            st, res = run_state(inst, "mbe", z, order="given", order_array=o, ibound_mode=mode)
+            check_tables(inst, st, run)
+            assert res.bound == run.bound and res.cost == run.cost
+            assert list(res.assignment) == list(run.sigma)
+
+
+def test_saturation_and_infeasible(orc):
+    # every joint row reaches the top cost: saturated tables, argmin 0
+    inst = synth.random_small(5, n=6, dmax=3, n_funcs=10, max_arity=3, p_top=0.9, top_k=50, hi=40)
+    o, _ = orc.minfill(inst)
+    run = orc.eliminate(inst, o, "be")
+    st, res = run_state(inst, "be", order="given", order_array=o)
+    check_tables(inst, st, run)
+    assert res.bound == run.bound
+
+
+def test_degenerate_problems(orc):
+    # no variables, only constants, an unconstrained variable, a single variable
+    empty = synth.Instance("empty", np.zeros(0, np.int32), [], [], "int", 1 << 30)
+    res = gb.be_solve(empty)
+    assert res.bound == 0 and res.cost == 0
+    consts = synth.Instance("c", np.array([3], np.int32), [np.zeros(0, np.int32)] * 2,
+                            [np.array([4]), np.array([5])], "int", 1 << 30)
+    res = gb.be_solve(consts)
+    assert res.bound == 9 and res.cost == 9 and list(res.assignment) == [0]
+    one = synth.Instance("one", np.array([5], np.int32), [np.array([0], np.int32)],
+                         [np.array([7, 3, 9, 3, 4])], "int", 1 << 30)
+    res = gb.be_solve(one)
+    assert res.bound == 3 and list(res.assignment) == [1]
+
+
+def test_components(orc):
+    a = synth.random_small(41, n=6, dmax=4, n_funcs=8, with_constant=False)
+    b = synth.random_small(42, n=5, dmax=4, n_funcs=7, with_constant=False)
+    a.top_k = b.top_k = 10**6
+    u = synth.disjoint_union(a, b)
+    ra, rb, ru = gb.be_solve(a), gb.be_solve(b), gb.be_solve(u)
+    assert ru.bound == ra.bound + rb.bound
+    assert ru.bound == orc.eliminate(u, orc.minfill(u)[0], "be").bound
+
+
+def test_config0_grid(orc):
+    for seed in range(3):
+        inst = synth.config_instance(0, seed)
+        o, w = orc.minfill(inst)
+        run = orc.eliminate(inst, o, "be")
+        for shape in (dict(), dict(batched=False), dict(use_graph=True)):
+            st, res = run_state(inst, "be", **shape)
+            check_tables(inst, st, run)
+            assert res.bound == run.bound == res.cost
+            assert list(res.assignment) == list(run.sigma)
+            assert res.induced_width == w == 4
+
+
+def test_config2_mbe_full(orc):
+    inst = synth.config_instance(2, 0)
+    o, _ = orc.minfill(inst)
+    run = orc.eliminate(inst, o, "log2", 16)
+    for shape in (dict(use_graph=True), dict(batched=False)):
+        st, res = run_state(inst, "mbe", 16, ibound_mode="log2", **shape)
+        check_tables(inst, st, run)
+        assert res.bound == run.bound and res.cost == run.cost
+        assert list(res.assignment) == list(run.sigma)
+
+
+def test_config3_mpe_mbe_and_exact_prefix(orc):
+    inst = synth.config_instance(3, 0)
+    o, _ = orc.minfill(inst)
+    orc.set_threads(orc.max_threads())
+    try:
+        run = orc.eliminate(inst, o, "sep", 20)
+    finally:
+        orc.set_threads(1)
+    st, res = run_state(inst, "mbe", 20, ibound_mode="sep", use_graph=True)
+    check_tables(inst, st, run, exact=False)
+    assert fp_close(res.bound, run.bound)
+    # the GPU's own assignment, re-evaluated in fp64 by the oracle
+    assert fp_close(res.cost, orc.evaluate(inst, res.assignment))
+    assert res.bound <= orc.evaluate(inst, res.assignment) + 1e-4 * (1 + abs(res.bound))
+    pre = synth.bn_prefix(inst, 60)
+    po, _ = orc.minfill(pre)
+    prun = orc.eliminate(pre, po, "be")
+    st, res = run_state(pre, "be")
+    check_tables(pre, st, prun, exact=False)
+    assert fp_close(res.bound, prun.bound)
+    assert fp_close(orc.evaluate(pre, res.assignment), prun.bound)
+
+
+def test_real_small_bruteforce(orc):
+    for seed in range(6):
+        inst = synth.random_small(seed + 900, n=7, dmax=4, n_funcs=10, cost_type="real")
+        best, _ = orc.bruteforce(inst)
+        res = gb.be_solve(inst)
+        assert fp_close(res.bound, best)
+        assert fp_close(orc.evaluate(inst, res.assignment), best)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_dpop_util_value(orc, seed):
+    inst = synth.dcop_random(seed, n_range=(20, 40), d_range=(3, 5), sep_cap=4)
+    st = gb.dpop_util(inst, inst.parent)
+    res = st.value()
+    o = orc.pseudotree_order(inst, inst.parent)
+    run = orc.eliminate(inst, o, "be")
+    check_tables(inst, st, run)
+    assert res.bound == run.bound == res.cost
+    assert list(res.assignment) == list(run.sigma)
+    st.free()
+    # the library's own DFS pseudo-tree
+    st = gb.dpop_util(inst)
+    res = st.value()
+    run = orc.eliminate(inst, orc.pseudotree_order(inst, orc.dfs_pseudotree(inst)), "be")
+    check_tables(inst, st, run)
+    assert res.bound == run.bound
+    st.free()
+
+
+def test_adpop_mbe_on_pseudotree_order(orc):
+    inst = synth.dcop_random(7, n_range=(25, 35), d_range=(3, 4), sep_cap=5)
+    o = orc.pseudotree_order(inst, inst.parent)
+    run = orc.eliminate(inst, o, "sep", 2)
+    st, res = run_state(inst, "mbe", 2, order="pseudotree", parent=inst.parent, ibound_mode="sep")
+    check_tables(inst, st, run)
+    assert res.bound == run.bound and res.cost == run.cost
+
+
+def test_rerun_is_idempotent(orc):
+    inst = synth.config_instance(0, 1)
+    st = gb.UtilState(inst, "be", use_graph=True)
+    st.bind()
+    outs = []
+    for _ in range(3):
+        st.run()
+        res = st.value()
+        outs.append((res.bound, tuple(res.assignment), tuple(st.fetch(len(st.tasks()) - 2)[0])))
+    assert outs[0] == outs[1] == outs[2]
+
+
+def test_autotune_keeps_parity(orc, tmp_path):
+    inst = synth.config_instance(2, 1)
+    o, _ = orc.minfill(inst)
+    run = orc.eliminate(inst, o, "log2", 12)
+    st = gb.UtilState(inst, "mbe", 12, ibound_mode="log2", use_graph=True,
+                      autotune_cache=str(tmp_path / "tune.txt"))
+    st.bind()
+    th, rp = st.autotune()
+    assert th in (128, 256, 512) and rp > 0
+    st.run()
+    res = st.value()
+    check_tables(inst, st, run)
+    assert res.bound == run.bound
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_util_bucket_entry(orc, seed):
+    import torch
+    rng = np.random.default_rng(seed)
+    m = int(rng.integers(0, 6))
+    sep_dom = [int(x) for x in rng.integers(1, 6, size=m)]
+    d = int(rng.integers(1, 9))
+    is_int = seed % 2 == 0
+    tables, positions, dev = [], [], []
+    for _ in range(int(rng.integers(1, 6))):
+        pos = sorted(int(x) for x in rng.choice(m, size=int(rng.integers(0, m + 1)), replace=False)) if m else []
+        size = int(np.prod([sep_dom[p] for p in pos])) * d if pos else d
+        if is_int:
+            t = rng.integers(0, 1000, size=size).astype(np.int32)
+        else:
+            t = (-np.log(rng.uniform(0.01, 1, size=size))).astype(np.float32)
+        tables.append(t.astype(np.float64))
+        positions.append(pos)
+        dev.append(torch.from_numpy(t).cuda())
+    rows = int(np.prod(sep_dom)) if m else 1
+    out = torch.zeros(rows, dtype=torch.int32 if is_int else torch.float32, device="cuda")
+    arg = torch.zeros(rows, dtype=torch.uint8, device="cuda")
+    gb.util_bucket(sep_dom, d, dev, positions, out, arg, "int" if is_int else "real", 1 << 30)
+    torch.cuda.synchronize()
+    want, warg = orc.util_bucket(sep_dom, d, tables, positions, is_int, 1 << 30)
+    if is_int:
+        assert np.array_equal(out.cpu().numpy().astype(np.float64), want)
+        assert np.array_equal(arg.cpu().numpy(), warg)
+    else:
+        assert fp_close(out.cpu().numpy(), want)
