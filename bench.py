@@ -1,0 +1,375 @@
+"""Benchmark of the GB300 UTIL-table library.
+
+Headline workload: exact Bucket Elimination on the 12x12 grid WCSP (144
+variables, domain 4, binary int32 tables U[0,1000], natural order, induced
+width 12, largest bucket table 4^13 joint entries).  One step = the whole hot
+path on device-resident tables: every bucket function (UTIL kernel, one
+persistent launch per elimination-tree level, replayed from a CUDA graph),
+the root reduction and the VALUE phase.  Metric: UTIL entries per second
+(joint separator x eliminated-variable rows of every bucket).
+
+Also reported on the same line: the HBM roofline of the UTIL kernel, the
+end-to-end solve through the C ABI from host buffers (wcsp_load + be_solve,
+uploads and result copy included), the oracle on the host cores, and the
+secondary workloads (level-batched vs per-bucket MBE on the Erdos-Renyi
+WCSP, MPE in the -log domain, DCOP serving latency).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU (torchrun): every rank solves its own instance (independent
+replicas, weak scaling); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "UTIL entries/s"
+UNIT = "entries/s"
+WORKLOAD = "BE 12x12 grid WCSP, d=4, int32 U[0,1000], natural order (w*=12, max table 4^13)"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_sample_instance():
+    """The first two rows of the headline grid (same tables, same order): a
+    bounded piece of the same workload for the oracle."""
+    import synth
+    inst = synth.config_instance(1, 0)
+    keep = [j for j, s in enumerate(inst.scopes) if int(np.max(s)) < 24]
+    return synth.Instance("grid12x12_rows0-1", inst.dom[:24].copy(), [inst.scopes[j] for j in keep],
+                          [inst.tables[j] for j in keep], "int", inst.top_k)
+
+
+def cpu_oracle_step():
+    """One oracle pass over the bounded sample; returns (entries, seconds, threads)."""
+    import oracle
+    inst = cpu_sample_instance()
+    th = oracle.max_threads()
+    oracle.set_threads(th)
+    t0 = time.perf_counter()
+    run = oracle.eliminate(inst, np.arange(inst.n), "be", tables=False)
+    dt = time.perf_counter() - t0
+    entries = sum(int(t.rows) * int(inst.dom[t.var]) for t in run.tasks)
+    return entries, dt, th
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_oracle_step()
+    tot_e, tot_t, th = 0, 0.0, 1
+    for _ in range(args.steps):
+        e, t, th = cpu_oracle_step()
+        tot_e += e
+        tot_t += t
+    v = tot_e / tot_t
+    sample = "oracle BE on rows 0-1 of the 12x12 grid (24 variables, natural order), every step"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": th, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def secondary(torch, gb, synth, steps):
+    """Batched vs per-bucket MBE (Erdos-Renyi), MPE entries/s, DCOP serving."""
+    out = {}
+    # level-batched (graph) vs one launch per bucket, MBE log2 <= 16
+    inst = synth.config_instance(2, 0)
+    times = {}
+    for name, kw in (("batched", dict(batched=True, use_graph=True)),
+                     ("plain", dict(batched=False, use_graph=False))):
+        st = gb.UtilState(inst, "mbe", 16, ibound_mode="log2", **kw)
+        st.bind()
+        ms = []
+        for k in range(3 + steps):
+            st.run()
+            st.sync()
+            if k >= 3:
+                ms.append(st.times()[0])
+        times[name] = statistics.median(ms)
+        info = st.info()
+        st.free()
+    out["mbe_er500"] = {"workload": "MBE Erdos-Renyi n=500, 1500 ternary tables, log2 bound 16",
+                        "tasks": info["n_tasks"], "levels": info["n_levels"],
+                        "util_entries": info["util_entries"],
+                        "batched_ms": times["batched"], "plain_ms": times["plain"],
+                        "batched_speedup": times["plain"] / times["batched"]}
+    # MPE, -log p in fp32, MBE i = 20
+    inst = synth.config_instance(3, 0)
+    st = gb.UtilState(inst, "mbe", 20, ibound_mode="sep", use_graph=True)
+    st.bind()
+    ms = []
+    for k in range(2 + steps):
+        st.run()
+        st.sync()
+        if k >= 2:
+            ms.append(st.times()[0])
+    info = st.info()
+    st.free()
+    m = statistics.median(ms)
+    out["mpe_bn200"] = {"workload": "MPE Bayesian network n=200, MBE i=20 (fp32 -log p)",
+                        "util_entries": info["util_entries"], "util_ms": m,
+                        "entries_per_s": info["util_entries"] / (m * 1e-3),
+                        "gbs": info["alg_bytes"] / (m * 1e-3) / 1e9}
+    out["serving"] = serve_bench(torch, gb, synth, int(os.environ.get("GPUBE_SERVE_REQUESTS", "400")))
+    return out
+
+
+def serve_bench(torch, gb, synth, n_req):
+    """Poisson stream of DCOPs through the continuous-batching server."""
+    insts = [synth.dcop_random(1000 + i) for i in range(n_req)]
+    loaded = [gb.WCSP(x) for x in insts]
+    budget = 8 << 30
+
+    def run(arrivals):
+        srv = gb.Server(budget, max_slots=64)
+        ids = {}
+        t0 = time.perf_counter()
+        nxt = 0
+        lag = {}
+        while True:
+            now = time.perf_counter() - t0
+            while nxt < n_req and arrivals[nxt] <= now:
+                rid = srv.submit(loaded[nxt], "dpop", parent=insts[nxt].parent)
+                ids[nxt] = rid
+                lag[nxt] = (time.perf_counter() - t0) - arrivals[nxt]
+                nxt += 1
+            left = srv.step()
+            if nxt >= n_req and left == 0:
+                break
+        wall = time.perf_counter() - t0
+        lat = []
+        ent = 0
+        for i in range(n_req):
+            ts, ta, td = srv.times(ids[i])
+            lat.append(td - ts + lag[i])
+            ent += srv.result(ids[i]).util_entries
+        st = srv.stats()
+        srv.close()
+        return wall, lat, ent, st
+
+    # saturated: everything arrives at once
+    wall, lat, ent, st = run(np.zeros(n_req))
+    sat = n_req / wall
+    rate = 0.8 * sat
+    arrivals, _ = synth.dcop_stream(n_req, 7, rate)
+    wall2, lat2, ent2, st2 = run(arrivals)
+    return {"workload": f"{n_req} random DCOPs (20-200 agents, d 5-10, sep <= 8), DPOP UTIL+VALUE",
+            "saturated_instances_per_s": sat, "poisson_rate": rate,
+            "instances_per_s": n_req / wall2, "p50_ms": 1e3 * float(np.percentile(lat2, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat2, 99)), "entries_per_s": ent2 / wall2,
+            "merged_launches": st2["launches"], "max_inflight": st2["max_inflight"]}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-secondary", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_1608_05288_gb300 as gb
+    from paper_1608_05288_gb300 import _build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+        dist.barrier()
+        _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+
+    inst = synth.config_instance(1, seed=rank)  # one replica per rank
+    st = gb.UtilState(inst, "be", order="best", use_graph=True, device=local)
+    st.bind(device=local)
+    info = st.info()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        st.run()
+        st.value_launch()
+    st.sync()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)  # L2 flush between steps (outside the step's events)
+        ev[k][0].record(stream)
+        st.run()
+        ev[k][1].record(stream)
+        st.value_launch()
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    st.sync()
+    util_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    step_ms = [a.elapsed_time(c) for a, _, c in ev]
+    tot_s = sum(step_ms) * 1e-3
+    if world > 1:
+        t = torch.tensor([tot_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_s = float(t.item())
+    value = info["util_entries"] * world * args.steps / tot_s
+    res = st.value()
+    n_launch_step = info["n_levels"] + 1  # one UTIL launch per level + the VALUE kernel
+
+    # roofline of the UTIL kernel: algorithmic bytes / its device time
+    peak, peak_kind = _peaks()
+    util_s = sum(util_ms) * 1e-3 / args.steps
+    achieved = info["alg_bytes"] / util_s / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get("util_kernel_grid12_bytes_per_launch")
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                "alg_bytes_per_step": info["alg_bytes"], "launches_per_step": info["n_levels"]}
+    st.free()
+    del flush
+
+    # end to end through the C ABI from host buffers: load, plan, upload, UTIL,
+    # VALUE, result copy, in every step
+    arena = torch.empty(info["arena_bytes"] + 4096, dtype=torch.uint8, device=dev)
+    e2e_s = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        w = gb.WCSP(inst)
+        r = gb.be_solve(w, order="best", arena=arena.data_ptr(), arena_bytes=arena.numel(),
+                        stream=stream.cuda_stream, device=local)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            e2e_s.append(t1 - t0)
+        assert r.bound == res.bound
+    e2e_tot = sum(e2e_s)
+    if world > 1:
+        t = torch.tensor([e2e_tot], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+    h2d = sum(len(t) for t in inst.tables) * 4
+    e2e = {"value": info["util_entries"] * world * args.steps / e2e_tot, "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24 + 4 * inst.n,
+           "ms_per_step": 1e3 * e2e_tot / args.steps}
+    del arena
+
+    extra = {}
+    cpu = None
+    if rank == 0 and world == 1:
+        if not args.no_secondary:
+            extra = secondary(torch, gb, synth, max(3, min(args.steps, 10)))
+        e, t, th = cpu_oracle_step()
+        cpu = {"value": e / t, "unit": UNIT, "cores": th, "kind": "oracle",
+               "sample": "oracle BE on rows 0-1 of the 12x12 grid (24 variables, natural order, "
+                         f"{e} joint entries, {t:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "buckets": info["n_tasks"], "levels": info["n_levels"],
+                           "util_entries_per_step": info["util_entries"],
+                           "l2": "flushed between steps (512 MB write)",
+                           "parallelism": f"replicas x{world}", "bound": res.bound},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": n_launch_step * args.steps, "clocks": clk,
+                "util_ms_per_step": 1e3 * util_s, "secondary": extra}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -233,3 +233,57 @@ def eliminate(inst, order, mode="be", z=0, tables=True):
                    int(L.orc_run_width(h)))
     finally:
         L.orc_run_free(h)
+
+
+class Handle:
+    """A finished oracle run kept in C memory, read one table at a time
+    (for full-size comparisons that do not fit twice in host memory)."""
+
+    def __init__(self, inst, order, mode="be", z=0):
+        self.inst = inst
+        self.p = Problem(inst)
+        o = np.ascontiguousarray(order, dtype=np.int32)
+        self.h = lib().orc_eliminate(self.p.ref, _iptr(o), MODES[mode], int(z))
+
+    @property
+    def ntasks(self):
+        return lib().orc_run_ntasks(self.h)
+
+    @property
+    def bound(self):
+        return lib().orc_run_bound(self.h)
+
+    @property
+    def cost(self):
+        return lib().orc_run_cost(self.h)
+
+    def sigma(self):
+        s = np.zeros(max(self.inst.n, 1), dtype=np.int32)
+        lib().orc_run_sigma(self.h, _iptr(s))
+        return s[: self.inst.n]
+
+    def task(self, t, table=True):
+        var, ns, ni = C.c_int(), C.c_int(), C.c_int()
+        rows = C.c_longlong()
+        sep = np.zeros(max(self.inst.n, 1), dtype=np.int32)
+        ids = np.zeros(self.inst.n_funcs + self.inst.n + 8, dtype=np.int32)
+        lib().orc_run_task(self.h, int(t), C.byref(var), C.byref(ns), _iptr(sep), C.byref(ni),
+                           _iptr(ids), C.byref(rows))
+        T = Task(var.value, sep[: ns.value].copy(), ids[: ni.value].copy(), rows.value)
+        if table:
+            T.out = np.zeros(rows.value, dtype=np.float64)
+            T.arg = np.zeros(rows.value, dtype=np.uint8)
+            lib().orc_run_table(self.h, int(t), T.out.ctypes.data_as(C.POINTER(C.c_double)),
+                                T.arg.ctypes.data_as(C.POINTER(C.c_ubyte)))
+        return T
+
+    def close(self):
+        if self.h:
+            lib().orc_run_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -190,9 +190,12 @@ class UtilState:
 
     def __init__(self, problem, kind="be", i_bound=0, parent=None, **opts):
         self.w = _as_wcsp(problem)
+        k = {"be": KIND_BE, "mbe": KIND_MBE, "dpop": KIND_DPOP}[kind] if isinstance(kind, str) else kind
+        if k != KIND_DPOP and parent is not None:
+            opts.setdefault("parent", parent)  # the pseudo-tree of a GPUBE_ORDER_PSEUDOTREE order
+            parent = None
         self.opts = make_opts(**opts)
         self.arena_tensor = None
-        k = {"be": KIND_BE, "mbe": KIND_MBE, "dpop": KIND_DPOP}[kind] if isinstance(kind, str) else kind
         par = _i32(parent) if parent is not None else None
         self._par = par
         h = C.c_void_p()

@@ -12,8 +12,9 @@ FP_RTOL = 1e-4
 def fp_close(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
-    both_inf = np.isinf(a) & np.isinf(b)
-    ok = both_inf | (np.abs(a - b) <= FP_RTOL * (1.0 + np.abs(b)))
+    both_inf = np.isinf(a) & np.isinf(b) & (np.sign(a) == np.sign(b))
+    with np.errstate(invalid="ignore"):
+        ok = both_inf | (np.abs(a - b) <= FP_RTOL * (1.0 + np.abs(b)))
     return bool(np.all(ok))
 
 

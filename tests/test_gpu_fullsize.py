@@ -1,0 +1,42 @@
+"""Full-size parity on the 12x12 grid (144 variables, d = 4, natural order,
+induced width 12, largest bucket 4^13 joint entries) in the launch
+configuration the benchmark times (batched levels replayed from a CUDA
+graph): every one of the 144 bucket functions and argmin tables, the
+optimum, the assignment and its cost, bit for bit against the oracle."""
+import numpy as np
+import pytest
+
+import synth
+import paper_1608_05288_gb300 as gb
+
+pytestmark = pytest.mark.gpu
+
+
+def test_config1_grid_full_size(orc):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    inst = synth.config_instance(1, 0)
+    st = gb.UtilState(inst, "be", order="best", use_graph=True)
+    st.bind()
+    for _ in range(2):  # the benchmark replays the graph; compare after a replay
+        st.run()
+    res = st.value()
+    st.sync()
+    order = st.order()
+    assert list(order) == list(range(144)) and res.induced_width == 12
+    orc.set_threads(orc.max_threads())
+    try:
+        with orc.Handle(inst, order, "be") as h:
+            assert h.ntasks == 144
+            tasks = st.tasks()
+            for t in range(h.ntasks):
+                T = h.task(t)
+                assert int(T.var) == tasks[t]["var"] and list(T.sep) == list(tasks[t]["sep"])
+                cost, arg = st.fetch(t)
+                assert np.array_equal(cost.astype(np.float64), T.out), f"task {t}"
+                assert np.array_equal(arg, T.arg), f"task {t}"
+            assert res.bound == h.bound == res.cost == h.cost
+            assert list(res.assignment) == list(h.sigma())
+    finally:
+        orc.set_threads(1)
