@@ -93,14 +93,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
+CPU_ROWS = 4  # grid rows in the oracle's bounded sample
+
+
 def cpu_sample_instance():
-    """The first two rows of the headline grid (same tables, same order): a
-    bounded piece of the same workload for the oracle."""
+    """The first CPU_ROWS rows of the headline grid (same tables, same
+    natural order): a bounded piece of the same workload for the oracle."""
     import synth
     inst = synth.config_instance(1, 0)
-    keep = [j for j, s in enumerate(inst.scopes) if int(np.max(s)) < 24]
-    return synth.Instance("grid12x12_rows0-1", inst.dom[:24].copy(), [inst.scopes[j] for j in keep],
-                          [inst.tables[j] for j in keep], "int", inst.top_k)
+    nv = 12 * CPU_ROWS
+    keep = [j for j, s in enumerate(inst.scopes) if int(np.max(s)) < nv]
+    return synth.Instance(f"grid12x12_rows0-{CPU_ROWS - 1}", inst.dom[:nv].copy(),
+                          [inst.scopes[j] for j in keep], [inst.tables[j] for j in keep], "int",
+                          inst.top_k)
 
 
 def cpu_oracle_step():
@@ -128,7 +133,7 @@ def reference_arm(args):
         tot_e += e
         tot_t += t
     v = tot_e / tot_t
-    sample = "oracle BE on rows 0-1 of the 12x12 grid (24 variables, natural order), every step"
+    sample = f"oracle BE on rows 0-{CPU_ROWS - 1} of the 12x12 grid ({12 * CPU_ROWS} variables, natural order), every step"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
@@ -230,6 +235,43 @@ def serve_bench(torch, gb, synth, n_req):
             "merged_launches": st2["launches"], "max_inflight": st2["max_inflight"]}
 
 
+def bucket_case(args):
+    """The grid's largest bucket alone through util_bucket: separator of 12
+    variables (d = 4), inputs = the previous bucket function (the 12 lowest
+    joint digits), the edge to the next row (top digit, x) and the edge to the
+    right neighbour (second-lowest digit, x); 4^13 joint entries.  Used for
+    kernel profiles."""
+    import torch
+    import paper_1608_05288_gb300 as gb
+    from paper_1608_05288_gb300 import _build
+    _build.build()
+    g = torch.Generator(device="cuda").manual_seed(0)
+    m, d = 12, 4
+    msg = torch.randint(0, 12000, (4 ** 12,), dtype=torch.int32, device="cuda", generator=g)
+    f1 = torch.randint(0, 1000, (16,), dtype=torch.int32, device="cuda", generator=g)
+    f2 = torch.randint(0, 1000, (16,), dtype=torch.int32, device="cuda", generator=g)
+    out = torch.empty(4 ** 12, dtype=torch.int32, device="cuda")
+    arg = torch.empty(4 ** 12, dtype=torch.uint8, device="cuda")
+    pos = [list(range(1, 12)), [0], [11]]
+    tabs = [msg, f1, f2]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for _ in range(args.warmup):
+        gb.util_bucket([d] * m, d, tabs, pos, out, arg)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        ev[k][0].record()
+        gb.util_bucket([d] * m, d, tabs, pos, out, arg)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    alg = 4 * (4 ** 12 + 32) + 5 * 4 ** 12
+    peak, kind = _peaks()
+    print(json.dumps({"case": "bucket13", "ms": ms, "alg_bytes": alg, "gbs": alg / ms / 1e6,
+                      "frac": alg / ms / 1e6 / peak, "peak_kind": kind}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -237,9 +279,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--case", default="", choices=["", "bucket13"])
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.case == "bucket13":
+        return bucket_case(args)
 
     import torch
     import torch.distributed as dist
@@ -350,8 +395,8 @@ def main():
             extra = secondary(torch, gb, synth, max(3, min(args.steps, 10)))
         e, t, th = cpu_oracle_step()
         cpu = {"value": e / t, "unit": UNIT, "cores": th, "kind": "oracle",
-               "sample": "oracle BE on rows 0-1 of the 12x12 grid (24 variables, natural order, "
-                         f"{e} joint entries, {t:.1f} s)"}
+               "sample": f"oracle BE on rows 0-{CPU_ROWS - 1} of the 12x12 grid ({12 * CPU_ROWS} variables, "
+                         f"natural order, {e} joint entries, {t:.1f} s)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

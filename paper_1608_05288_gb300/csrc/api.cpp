@@ -264,7 +264,7 @@ static void layout(util_state *s)
     }
     for (Task &T : P.tasks) T.arg_off = c.take(T.rows, 128);
     for (Task &T : P.tasks) {
-        T.A_off = c.take(static_cast<size_t>(T.H) * T.sa * 4, 128);
+        T.A_off = c.take(static_cast<size_t>(T.G + 1) * T.sa * 4, 128);
         T.B_off = c.take(static_cast<size_t>(T.P_lo) * T.sb * 4, 128);
     }
     // the value plan refers to table offsets, so it is built after them
@@ -312,7 +312,7 @@ static void layout(util_state *s)
     // tables of BE / DPOP messages are released once their bucket is done
     size_t fixed = s->upload_bytes + (s->arena_bytes - s->desc_off);
     size_t live = fixed, peak = fixed;
-    for (const Task &T : P.tasks) live += al(T.rows, 128) + al(T.H * T.sa * 4, 128) + al(T.P_lo * T.sb * 4, 128);
+    for (const Task &T : P.tasks) live += al(T.rows, 128) + al((T.G + 1) * T.sa * 4, 128) + al(T.P_lo * T.sb * 4, 128);
     peak = live;
     for (const Task &T : P.tasks) {
         live += al(T.rows * 4, 128);
@@ -456,14 +456,19 @@ static int build_descriptors(util_state *s)
         x.sa = T.sa;
         x.sb = T.sb;
         x.P_lo = static_cast<int32_t>(T.P_lo);
-        x.H = static_cast<int32_t>(T.H);
-        x.hc = static_cast<int32_t>(std::min<int64_t>(std::max(s->cfg.rows_per_item, 1), T.H));
+        x.G = static_cast<int32_t>(T.G);
+        x.R0 = T.R0;
+        // rows_per_item counts separator rows; an item spans whole groups
+        const int64_t groups = std::max<int64_t>(1, s->cfg.rows_per_item / std::max(T.R0, 1));
+        x.hc = static_cast<int32_t>(std::min<int64_t>(groups, T.G));
         x.nlc = static_cast<int32_t>((T.P_lo + NT - 1) / NT);
-        const int64_t items = static_cast<int64_t>(x.nlc) * ((T.H + x.hc - 1) / x.hc);
+        const int64_t items = static_cast<int64_t>(x.nlc) * ((T.G + x.hc - 1) / x.hc);
         if (items > INT32_MAX / 2) return set_error(GPUBE_ENOMEM, "task %d has too many work items", t);
         x.n_items = static_cast<int32_t>(items);
         x.variant = dclass_of(T.d) * kNumFClass + fclass_of(x.F);
         x.stage_bytes = T.stage_bytes;
+        x.n_lo = T.n_lo;
+        x.n_gi = T.n_gi;
         for (size_t f = 0; f < T.inputs.size(); ++f) {
             InDev &in = ind[in_pos + f];
             in.ptr = func_ptr(s, T.inputs[f]);
@@ -544,7 +549,7 @@ static int build_descriptors(util_state *s)
         x.F = static_cast<int32_t>(T.inputs.size());
         x.sa = T.sa;
         x.sb = T.sb;
-        x.H = static_cast<int32_t>(T.H);
+        x.G = static_cast<int32_t>(T.G);
         x.P_lo = static_cast<int32_t>(T.P_lo);
         x.rad_off = static_cast<int32_t>(po);
         for (int j = 0; j < m; ++j) pool[po++] = w.dom[T.sep[j]];
@@ -554,7 +559,7 @@ static int build_descriptors(util_state *s)
         task_strides(w, P, T, st);
         for (int32_t v : st) pool[po++] = v;
         exp_pre[t] = tot;
-        tot += T.H + T.P_lo;
+        tot += T.G + 1 + T.P_lo;
     }
     exp_pre[nt] = tot;
     // value plan
@@ -1063,7 +1068,7 @@ extern "C" int util_bucket(int32_t cost_type, int32_t top_k, int32_t m, const in
         if (e == cudaSuccess)
             e = launch_expand(reinterpret_cast<const ExpandDev *>(s.base + D.expand),
                               reinterpret_cast<const int64_t *>(s.base + D.exp_prefix), 1,
-                              P.tasks[0].H + P.tasks[0].P_lo, reinterpret_cast<const int32_t *>(s.base + D.pool),
+                              P.tasks[0].G + 1 + P.tasks[0].P_lo, reinterpret_cast<const int32_t *>(s.base + D.pool),
                               s.num_sms, s.stream);
         if (e != cudaSuccess) rc = cuda_error(e, "util_bucket upload");
         else rc = enqueue_util(&s, s.stream);

@@ -17,10 +17,14 @@ constexpr int kStatusTimeout = 1;
 
 // Kernel variants: the eliminated domain class times the input-count class.
 // D class 0 = any domain size (runtime loop); 1..7 = domain 2..8.
-// F class 0..2 = at most 4 or 8 inputs held in registers; 2 = any count.
+// F class 0..2 = at most 3 or 7 inputs held in registers (A rows of 4 or 8
+// ints, B rows of 4 or 8 ints); 2 = any count.
 constexpr int kNumFClass = 3;
 inline int dclass_of(int d) { return (d >= 2 && d <= 8) ? d - 1 : 0; }
-inline int fclass_of(int F) { return F <= 4 ? 0 : F <= 8 ? 1 : 2; }
+inline int fclass_of(int F) { return F <= 3 ? 0 : F <= 7 ? 1 : 2; }
+// Row widths of the A (output + inputs) and B (inputs) offset tables.
+inline int arow_of(int F) { return F <= 3 ? 4 : F <= 7 ? 8 : (F + 1 + 3) / 4 * 4; }
+inline int brow_of(int F) { return F <= 3 ? 4 : F <= 7 ? 8 : (F + 3) / 4 * 4; }
 
 // One input of a (mini-)bucket.
 struct alignas(16) InDev {
@@ -33,21 +37,29 @@ struct alignas(16) InDev {
 //
 // Its output rows r (the separator assignments, row-major) are split as
 // r = hi * P_lo + lo: lo enumerates the lowest separator digits, hi the
-// others.  For input f the row offset of x_i's d contiguous entries is
-// A[h][f] + B[lo][f], where h is hi's index in the task's chosen iteration
-// order and A[h][F] is the output offset of (hi, lo = 0).
+// others.  The hi values are walked in a planner-chosen digit order whose
+// fastest digit u (radix R0) is one the largest input does not mention; the
+// other hi digits form the group index g.  For input f the row offset of
+// x_i's d contiguous entries is A[g][1 + f] + u * A[G][1 + f] + B[lo][f]
+// (row G of A holds the per-slot stride of u), and the output row is
+// A[g][0] + u * A[G][0] + lo.  Inputs are ordered: n_lo that mention no hi
+// digit (summed once per item), then up to n_gi that do not mention u
+// (read once per group), then the rest (read per row).
 struct alignas(16) TaskDev {
-    const int32_t *A;    // [H][sa]
+    const int32_t *A;    // [G + 1][sa]
     const int32_t *B;    // [P_lo][sb]
     const InDev *in;     // [F]
     void *out;           // [rows] int32 or float
     uint8_t *arg;        // [rows]
     int32_t F, d, sa, sb;
-    int32_t P_lo, H, hc, nlc;  // nlc = lo chunks of blockDim.x rows
+    int32_t P_lo, G, hc, nlc;  // hc = groups per item; nlc = lo chunks of blockDim.x rows
     int32_t variant;           // dclass * kNumFClass + fclass
     int32_t stage_bytes;       // sum of staged bytes (multiple of 16)
-    int32_t n_items;           // nlc * ceil(H / hc)
-    int32_t pad;
+    int32_t n_items;           // nlc * ceil(G / hc)
+    int32_t n_lo;              // inputs [0, n_lo) depend on lo only
+    int32_t n_gi;              // inputs [n_lo, n_gi) do not depend on u
+    int32_t R0;                // radix of u (1 when there is no hi digit)
+    int32_t pad0, pad1;
 };
 
 // One kernel launch: a list of tasks whose work items are handed out by an
@@ -69,10 +81,10 @@ struct alignas(16) ExpandDev {
     int32_t *B;
     int32_t m, L, nh, F;    // separator digits, lo digits, hi digits, inputs
     int32_t sa, sb;
-    int32_t H, P_lo;
+    int32_t G, P_lo;        // groups (hi values / R0), lo extent
     int32_t rad_off;        // pool offset of rad[m] (natural digit order, slowest first)
     int32_t perm_off;       // pool offset of hperm[nh] (hi digits, fastest first)
-    int32_t stride_off;     // pool offset of stride[(F + 1) * m] (slot F = output)
+    int32_t stride_off;     // pool offset of stride[(F + 1) * m] (row F = output)
     int32_t pad;
 };
 

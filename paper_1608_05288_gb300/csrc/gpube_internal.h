@@ -61,8 +61,12 @@ struct Task {
     size_t out_off = 0, arg_off = 0;
     // work decomposition (see TaskDev)
     int32_t L = 0;                 // lo digits (the lowest separator digits)
-    int64_t P_lo = 1, H = 1;
+    int64_t P_lo = 1, H = 1;       // lo extent, hi extent
+    int64_t G = 1;                 // groups = H / R0
+    int32_t R0 = 1;                // radix of the fastest hi digit
+    int32_t n_gi = 0;              // inputs [n_lo, n_gi) do not mention the fastest hi digit
     int32_t sa = 4, sb = 4;
+    int32_t n_lo = 0;              // leading inputs that depend on lo digits only
     std::vector<int32_t> hperm;    // hi digit indices, fastest first
     size_t A_off = 0, B_off = 0;
     void *ext_out = nullptr;       // caller's output tables (single-bucket calls)
@@ -93,7 +97,7 @@ struct Plan {
 // Launch parameters of one run.
 struct LaunchCfg {
     int32_t threads = 256;
-    int32_t rows_per_item = 16;
+    int32_t rows_per_item = 32;
 };
 
 // planner (plan.cpp)

@@ -463,8 +463,9 @@ void task_strides(const wcsp &w, const Plan &P, const Task &T, std::vector<int32
     }
 }
 
-// Split every task's rows into (hi, lo), choose the hi iteration order and
-// the staged inputs.
+// Split every task's rows into (hi, lo), choose the hi iteration order
+// (its fastest digit u, then the groups), order the inputs by how often
+// they are read, and choose the staged inputs.
 void shape_tasks(const wcsp &w, Plan &P)
 {
     for (Task &T : P.tasks) {
@@ -477,8 +478,8 @@ void shape_tasks(const wcsp &w, Plan &P)
             T.L++;
         }
         T.H = T.rows / T.P_lo;
-        // hi digits absent from the largest input iterate fastest: a thread's
-        // consecutive rows then reread the same input entries
+        // hi digits absent from the largest input iterate fastest: consecutive
+        // rows then share that input's entries
         int big = 0;
         for (int f = 1; f < F; ++f)
             if (P.funcs[T.inputs[f]].size > P.funcs[T.inputs[big]].size) big = f;
@@ -490,8 +491,28 @@ void shape_tasks(const wcsp &w, Plan &P)
         }
         T.hperm = absent;
         T.hperm.insert(T.hperm.end(), present.begin(), present.end());
-        T.sa = static_cast<int32_t>(align_up(F + 1, 4));
-        T.sb = static_cast<int32_t>(align_up(std::max(F, 1), 4));
+        T.R0 = T.hperm.empty() ? 1 : w.dom[T.sep[T.hperm[0]]];
+        T.G = T.H / T.R0;
+        // inputs: lo digits only | hi digits but not u | u
+        {
+            std::vector<int32_t> lo_only, group, row;
+            for (int fid : T.inputs) {
+                const auto &fs = P.funcs[fid].scope;
+                auto has = [&](int j) { return std::find(fs.begin(), fs.end(), T.sep[j]) != fs.end(); };
+                bool hi = false;
+                for (int j = 0; j < m - T.L && !hi; ++j) hi = has(j);
+                if (!hi) lo_only.push_back(fid);
+                else if (!has(T.hperm[0])) group.push_back(fid);
+                else row.push_back(fid);
+            }
+            T.n_lo = static_cast<int32_t>(lo_only.size());
+            T.n_gi = static_cast<int32_t>(lo_only.size() + group.size());
+            T.inputs = lo_only;
+            T.inputs.insert(T.inputs.end(), group.begin(), group.end());
+            T.inputs.insert(T.inputs.end(), row.begin(), row.end());
+        }
+        T.sa = arow_of(F);
+        T.sb = brow_of(F);
         // stage the smallest inputs while they fit
         T.stage_off.assign(F, -1);
         T.stage_bytes = 0;

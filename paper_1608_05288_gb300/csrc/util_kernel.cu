@@ -152,44 +152,66 @@ __device__ __forceinline__ const T *input_base(const InDev &in, const unsigned c
 }
 
 // --------------------------------------------------------- item bodies
-// Fixed domain D, at most FC inputs (offsets held in registers).
+template <int N>
+__device__ __forceinline__ void load_ints(const int32_t *p, int32_t (&a)[N])
+{
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+        const int4 x = reinterpret_cast<const int4 *>(p)[i];
+        a[4 * i + 0] = x.x;
+        a[4 * i + 1] = x.y;
+        a[4 * i + 2] = x.z;
+        a[4 * i + 3] = x.w;
+    }
+}
+
+// Fixed domain D, at most FC inputs (FC = 3 or 7: A rows of FC + 1 ints,
+// one or two 16-byte loads).  Lo-only inputs are summed once per item;
+// group inputs once per group, two groups at a time so that two independent
+// loads of the large input are in flight per thread; the other inputs per
+// row.
 template <typename T, int D, int FC>
 __device__ __forceinline__ void item_fixed(const TaskDev &tk, const unsigned char *stage, int lo,
-                                           int h0, int h1, uint32_t k)
+                                           int g0, int g1, uint32_t k)
 {
     using C = Cost<T>;
     using A = typename C::acc;
-    const int F = tk.F;
+    constexpr int SA = FC + 1;
+    constexpr int SB = (FC + 3) / 4 * 4;
+    const int F = tk.F, nlo = tk.n_lo, ngi = tk.n_gi, R0 = tk.R0;
+    int32_t b[SB];
+    load_ints<SB>(tk.B + static_cast<int64_t>(lo) * SB, b);
     const T *p[FC];
-    int32_t bo[FC];
-    const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * tk.sb;
 #pragma unroll
-    for (int f = 0; f < FC; ++f) {
-        if (f < F) {
-            p[f] = input_base<T>(tk.in[f], stage);
-            bo[f] = Brow[f];
-        } else {
-            p[f] = nullptr;
-            bo[f] = 0;
+    for (int f = 0; f < FC; ++f) p[f] = (f < F) ? input_base<T>(tk.in[f], stage) + b[f] : nullptr;
+    A base[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) base[l] = A(0);
+#pragma unroll
+    for (int f = 0; f < FC; ++f)
+        if (f < nlo) {
+            T v[D];
+            load_run<D>(p[f], v);
+#pragma unroll
+            for (int l = 0; l < D; ++l) base[l] = C::add(base[l], v[l], k);
         }
-    }
+    int32_t du[SA];
+    load_ints<SA>(tk.A + static_cast<int64_t>(tk.G) * SA, du);
     T *out = static_cast<T *>(tk.out);
     uint8_t *arg = tk.arg;
-    for (int h = h0; h < h1; ++h) {
-        const int32_t *Ar = tk.A + static_cast<int64_t>(h) * tk.sa;
-        T v[D];
+
+    auto row = [&](const int32_t (&a)[SA], const A (&pre)[D], int u) {
         A acc[D];
-        load_run<D>(p[0] + (Ar[0] + bo[0]), v);
 #pragma unroll
-        for (int l = 0; l < D; ++l) acc[l] = C::from(v[l]);
+        for (int l = 0; l < D; ++l) acc[l] = pre[l];
 #pragma unroll
-        for (int f = 1; f < FC; ++f) {
-            if (f < F) {
-                load_run<D>(p[f] + (Ar[f] + bo[f]), v);
+        for (int f = 0; f < FC; ++f)
+            if (f >= ngi && f < F) {
+                T v[D];
+                load_run<D>(p[f] + (a[1 + f] + u * du[1 + f]), v);
 #pragma unroll
                 for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
             }
-        }
         A best = acc[0];
         int bi = 0;
 #pragma unroll
@@ -198,119 +220,154 @@ __device__ __forceinline__ void item_fixed(const TaskDev &tk, const unsigned cha
                 best = acc[l];
                 bi = l;
             }
-        const int o = Ar[F] + lo;
+        const int o = a[0] + u * du[0] + lo;
         out[o] = C::store(best);
         arg[o] = static_cast<uint8_t>(bi);
+    };
+
+    // NG groups at a time: their group-input loads are independent and in
+    // flight together (two for the narrow variants, one when registers are
+    // short)
+    constexpr int NG = (FC <= 3 && D <= 4) ? 2 : 1;
+    for (int g = g0; g < g1; g += NG) {
+        int32_t a[NG][SA];
+        A pre[NG][D];
+#pragma unroll
+        for (int j = 0; j < NG; ++j) {
+            load_ints<SA>(tk.A + static_cast<int64_t>(g + j < g1 ? g + j : g) * SA, a[j]);
+#pragma unroll
+            for (int l = 0; l < D; ++l) pre[j][l] = base[l];
+        }
+#pragma unroll
+        for (int f = 0; f < FC; ++f)
+            if (f >= nlo && f < ngi) {
+                T x[NG][D];
+#pragma unroll
+                for (int j = 0; j < NG; ++j) load_run<D>(p[f] + a[j][1 + f], x[j]);
+#pragma unroll
+                for (int j = 0; j < NG; ++j)
+#pragma unroll
+                    for (int l = 0; l < D; ++l) pre[j][l] = C::add(pre[j][l], x[j][l], k);
+            }
+        for (int u = 0; u < R0; ++u) {
+#pragma unroll
+            for (int j = 0; j < NG; ++j)
+                if (g + j < g1) row(a[j], pre[j], u);
+        }
     }
 }
 
 // Fixed domain D, any number of inputs (offsets reread per input).
 template <typename T, int D>
 __device__ __forceinline__ void item_fixed_anyF(const TaskDev &tk, const unsigned char *stage, int lo,
-                                                int h0, int h1, uint32_t k)
+                                                int g0, int g1, uint32_t k)
 {
     using C = Cost<T>;
     using A = typename C::acc;
     const int F = tk.F;
     const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * tk.sb;
+    const int32_t *du = tk.A + static_cast<int64_t>(tk.G) * tk.sa;
     T *out = static_cast<T *>(tk.out);
-    for (int h = h0; h < h1; ++h) {
-        const int32_t *Ar = tk.A + static_cast<int64_t>(h) * tk.sa;
-        T v[D];
-        A acc[D];
-        load_run<D>(input_base<T>(tk.in[0], stage) + (Ar[0] + Brow[0]), v);
+    for (int g = g0; g < g1; ++g) {
+        const int32_t *Ar = tk.A + static_cast<int64_t>(g) * tk.sa;
+        for (int u = 0; u < tk.R0; ++u) {
+            A acc[D];
 #pragma unroll
-        for (int l = 0; l < D; ++l) acc[l] = C::from(v[l]);
-        for (int f = 1; f < F; ++f) {
-            load_run<D>(input_base<T>(tk.in[f], stage) + (Ar[f] + Brow[f]), v);
+            for (int l = 0; l < D; ++l) acc[l] = A(0);
+            for (int f = 0; f < F; ++f) {
+                T v[D];
+                load_run<D>(input_base<T>(tk.in[f], stage) + (Ar[1 + f] + u * du[1 + f] + Brow[f]), v);
 #pragma unroll
-            for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
-        }
-        A best = acc[0];
-        int bi = 0;
-#pragma unroll
-        for (int l = 1; l < D; ++l)
-            if (acc[l] < best) {
-                best = acc[l];
-                bi = l;
+                for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
             }
-        const int o = Ar[F] + lo;
-        out[o] = C::store(best);
-        tk.arg[o] = static_cast<uint8_t>(bi);
+            A best = acc[0];
+            int bi = 0;
+#pragma unroll
+            for (int l = 1; l < D; ++l)
+                if (acc[l] < best) {
+                    best = acc[l];
+                    bi = l;
+                }
+            const int o = Ar[0] + u * du[0] + lo;
+            out[o] = C::store(best);
+            tk.arg[o] = static_cast<uint8_t>(bi);
+        }
     }
 }
 
 // Any domain size (runtime loop over x_i's values), at most FC inputs.
 template <typename T, int FC>
-__device__ __forceinline__ void item_anyD(const TaskDev &tk, const unsigned char *stage, int lo, int h0,
-                                          int h1, uint32_t k)
+__device__ __forceinline__ void item_anyD(const TaskDev &tk, const unsigned char *stage, int lo, int g0,
+                                          int g1, uint32_t k)
 {
     using C = Cost<T>;
     using A = typename C::acc;
+    constexpr int SA = FC + 1;
+    constexpr int SB = (FC + 3) / 4 * 4;
     const int F = tk.F, d = tk.d;
+    int32_t b[SB];
+    load_ints<SB>(tk.B + static_cast<int64_t>(lo) * SB, b);
+    int32_t du[SA];
+    load_ints<SA>(tk.A + static_cast<int64_t>(tk.G) * SA, du);
     const T *p[FC];
-    int32_t bo[FC];
-    const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * tk.sb;
 #pragma unroll
-    for (int f = 0; f < FC; ++f) {
-        if (f < F) {
-            p[f] = input_base<T>(tk.in[f], stage);
-            bo[f] = Brow[f];
-        } else {
-            p[f] = nullptr;
-            bo[f] = 0;
-        }
-    }
+    for (int f = 0; f < FC; ++f) p[f] = (f < F) ? input_base<T>(tk.in[f], stage) + b[f] : nullptr;
     T *out = static_cast<T *>(tk.out);
-    for (int h = h0; h < h1; ++h) {
-        const int32_t *Ar = tk.A + static_cast<int64_t>(h) * tk.sa;
-        const T *q[FC];
+    for (int g = g0; g < g1; ++g) {
+        int32_t a[SA];
+        load_ints<SA>(tk.A + static_cast<int64_t>(g) * SA, a);
+        for (int u = 0; u < tk.R0; ++u) {
+            const T *q[FC];
 #pragma unroll
-        for (int f = 0; f < FC; ++f) q[f] = (f < F) ? p[f] + (Ar[f] + bo[f]) : nullptr;
-        A best = C::from(q[0][0]);
-        int bi = 0;
-        for (int l = 0; l < d; ++l) {
-            A a = C::from(q[0][l]);
+            for (int f = 0; f < FC; ++f) q[f] = (f < F) ? p[f] + (a[1 + f] + u * du[1 + f]) : nullptr;
+            A best = A(0);
+            int bi = 0;
+            for (int l = 0; l < d; ++l) {
+                A s = C::from(q[0][l]);
 #pragma unroll
-            for (int f = 1; f < FC; ++f)
-                if (f < F) a = C::add(a, q[f][l], k);
-            if (l == 0 || a < best) {
-                best = a;
-                bi = l;
+                for (int f = 1; f < FC; ++f)
+                    if (f < F) s = C::add(s, q[f][l], k);
+                if (l == 0 || s < best) {
+                    best = s;
+                    bi = l;
+                }
             }
+            const int o = a[0] + u * du[0] + lo;
+            out[o] = C::store(best);
+            tk.arg[o] = static_cast<uint8_t>(bi);
         }
-        const int o = Ar[F] + lo;
-        out[o] = C::store(best);
-        tk.arg[o] = static_cast<uint8_t>(bi);
     }
 }
 
 // Any domain size, any number of inputs.
 template <typename T>
 __device__ __forceinline__ void item_anyD_anyF(const TaskDev &tk, const unsigned char *stage, int lo,
-                                               int h0, int h1, uint32_t k)
+                                               int g0, int g1, uint32_t k)
 {
     using C = Cost<T>;
     using A = typename C::acc;
     const int F = tk.F, d = tk.d;
     const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * tk.sb;
+    const int32_t *du = tk.A + static_cast<int64_t>(tk.G) * tk.sa;
     T *out = static_cast<T *>(tk.out);
-    for (int h = h0; h < h1; ++h) {
-        const int32_t *Ar = tk.A + static_cast<int64_t>(h) * tk.sa;
-        A best = A(0);
-        int bi = 0;
-        for (int l = 0; l < d; ++l) {
-            A a = C::from(input_base<T>(tk.in[0], stage)[Ar[0] + Brow[0] + l]);
-            for (int f = 1; f < F; ++f)
-                a = C::add(a, input_base<T>(tk.in[f], stage)[Ar[f] + Brow[f] + l], k);
-            if (l == 0 || a < best) {
-                best = a;
-                bi = l;
+    for (int g = g0; g < g1; ++g) {
+        const int32_t *Ar = tk.A + static_cast<int64_t>(g) * tk.sa;
+        for (int u = 0; u < tk.R0; ++u) {
+            A best = A(0);
+            int bi = 0;
+            for (int l = 0; l < d; ++l) {
+                A s = A(0);
+                for (int f = 0; f < F; ++f)
+                    s = C::add(s, input_base<T>(tk.in[f], stage)[Ar[1 + f] + u * du[1 + f] + Brow[f] + l], k);
+                if (l == 0 || s < best) {
+                    best = s;
+                    bi = l;
+                }
             }
+            const int o = Ar[0] + u * du[0] + lo;
+            out[o] = C::store(best);
+            tk.arg[o] = static_cast<uint8_t>(bi);
         }
-        const int o = Ar[F] + lo;
-        out[o] = C::store(best);
-        tk.arg[o] = static_cast<uint8_t>(bi);
     }
 }
 
@@ -320,14 +377,14 @@ __device__ __forceinline__ void dispatch_f(const TaskDev &tk, int fc, const unsi
 {
     if constexpr (D == 0) {
         switch (fc) {
-        case 0: item_anyD<T, 4>(tk, stage, lo, h0, h1, k); break;
-        case 1: item_anyD<T, 8>(tk, stage, lo, h0, h1, k); break;
+        case 0: item_anyD<T, 3>(tk, stage, lo, h0, h1, k); break;
+        case 1: item_anyD<T, 7>(tk, stage, lo, h0, h1, k); break;
         default: item_anyD_anyF<T>(tk, stage, lo, h0, h1, k); break;
         }
     } else {
         switch (fc) {
-        case 0: item_fixed<T, D, 4>(tk, stage, lo, h0, h1, k); break;
-        case 1: item_fixed<T, D, 8>(tk, stage, lo, h0, h1, k); break;
+        case 0: item_fixed<T, D, 3>(tk, stage, lo, h0, h1, k); break;
+        case 1: item_fixed<T, D, 7>(tk, stage, lo, h0, h1, k); break;
         default: item_fixed_anyF<T, D>(tk, stage, lo, h0, h1, k); break;
         }
     }
@@ -410,7 +467,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
         const int hr = local / tk.nlc;
         const int lc = local - hr * tk.nlc;
         const int h0 = hr * tk.hc;
-        const int h1 = min(h0 + tk.hc, tk.H);
+        const int h1 = min(h0 + tk.hc, tk.G);
         const int lo = lc * blockDim.x + tid;
         if (lo < tk.P_lo) dispatch<T>(tk, stage, lo, h0, h1, L.top_k);
 
@@ -440,19 +497,31 @@ __global__ void expand_kernel(const ExpandDev *tasks, const int64_t *prefix, int
         const int32_t *perm = pool + x.perm_off;
         const int32_t *st = pool + x.stride_off;
         int64_t r = e - prefix[a];
-        if (r < x.H) {
+        if (r <= x.G) {
+            // group rows: the hi digits other than the fastest one (perm[0]);
+            // row G: the strides of perm[0] (zero when there is no hi digit)
             int32_t *row = x.A + r * x.sa;
             for (int f = 0; f < x.sa; ++f) row[f] = 0;
-            int64_t h = r;
-            for (int i = 0; i < x.nh; ++i) {
-                const int j = perm[i];
-                const int dig = static_cast<int>(h % rad[j]);
-                h /= rad[j];
-                if (dig)
-                    for (int f = 0; f <= x.F; ++f) row[f] += dig * st[f * x.m + j];
+            if (r == x.G) {
+                if (x.nh > 0) {
+                    const int j = perm[0];
+                    row[0] = st[x.F * x.m + j];
+                    for (int f = 0; f < x.F; ++f) row[1 + f] = st[f * x.m + j];
+                }
+            } else {
+                int64_t h = r;
+                for (int i = 1; i < x.nh; ++i) {
+                    const int j = perm[i];
+                    const int dig = static_cast<int>(h % rad[j]);
+                    h /= rad[j];
+                    if (dig) {
+                        row[0] += dig * st[x.F * x.m + j];
+                        for (int f = 0; f < x.F; ++f) row[1 + f] += dig * st[f * x.m + j];
+                    }
+                }
             }
         } else {
-            const int64_t lo = r - x.H;
+            const int64_t lo = r - x.G - 1;
             int32_t *row = x.B + lo * x.sb;
             for (int f = 0; f < x.sb; ++f) row[f] = 0;
             int64_t q = lo;
