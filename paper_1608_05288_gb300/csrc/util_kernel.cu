@@ -114,6 +114,8 @@ template <> struct Cost<float> {
     static __device__ __forceinline__ float store(acc a) { return a; }
 };
 
+template <typename T> using A_t = typename Cost<T>::acc;
+
 // The d entries of one x_i-run, loaded with the widest aligned vector:
 // offsets are multiples of d, so d % 4 == 0 runs are 16-byte aligned.
 template <int D, typename T>
@@ -165,98 +167,6 @@ __device__ __forceinline__ void load_ints(const int32_t *p, int32_t (&a)[N])
     }
 }
 
-// Fixed domain D, at most FC inputs (FC = 3 or 7: A rows of FC + 1 ints,
-// one or two 16-byte loads).  Lo-only inputs are summed once per item;
-// group inputs once per group, two groups at a time so that two independent
-// loads of the large input are in flight per thread; the other inputs per
-// row.
-template <typename T, int D, int FC>
-__device__ __forceinline__ void item_fixed(const TaskDev &tk, const unsigned char *stage, int lo,
-                                           int g0, int g1, uint32_t k)
-{
-    using C = Cost<T>;
-    using A = typename C::acc;
-    constexpr int SA = FC + 1;
-    constexpr int SB = (FC + 3) / 4 * 4;
-    const int F = tk.F, nlo = tk.n_lo, ngi = tk.n_gi, R0 = tk.R0;
-    int32_t b[SB];
-    load_ints<SB>(tk.B + static_cast<int64_t>(lo) * SB, b);
-    const T *p[FC];
-#pragma unroll
-    for (int f = 0; f < FC; ++f) p[f] = (f < F) ? input_base<T>(tk.in[f], stage) + b[f] : nullptr;
-    A base[D];
-#pragma unroll
-    for (int l = 0; l < D; ++l) base[l] = A(0);
-#pragma unroll
-    for (int f = 0; f < FC; ++f)
-        if (f < nlo) {
-            T v[D];
-            load_run<D>(p[f], v);
-#pragma unroll
-            for (int l = 0; l < D; ++l) base[l] = C::add(base[l], v[l], k);
-        }
-    int32_t du[SA];
-    load_ints<SA>(tk.A + static_cast<int64_t>(tk.G) * SA, du);
-    T *out = static_cast<T *>(tk.out);
-    uint8_t *arg = tk.arg;
-
-    auto row = [&](const int32_t (&a)[SA], const A (&pre)[D], int u) {
-        A acc[D];
-#pragma unroll
-        for (int l = 0; l < D; ++l) acc[l] = pre[l];
-#pragma unroll
-        for (int f = 0; f < FC; ++f)
-            if (f >= ngi && f < F) {
-                T v[D];
-                load_run<D>(p[f] + (a[1 + f] + u * du[1 + f]), v);
-#pragma unroll
-                for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
-            }
-        A best = acc[0];
-        int bi = 0;
-#pragma unroll
-        for (int l = 1; l < D; ++l)
-            if (acc[l] < best) {
-                best = acc[l];
-                bi = l;
-            }
-        const int o = a[0] + u * du[0] + lo;
-        out[o] = C::store(best);
-        arg[o] = static_cast<uint8_t>(bi);
-    };
-
-    // NG groups at a time: their group-input loads are independent and in
-    // flight together (two for the narrow variants, one when registers are
-    // short)
-    constexpr int NG = (FC <= 3 && D <= 4) ? 2 : 1;
-    for (int g = g0; g < g1; g += NG) {
-        int32_t a[NG][SA];
-        A pre[NG][D];
-#pragma unroll
-        for (int j = 0; j < NG; ++j) {
-            load_ints<SA>(tk.A + static_cast<int64_t>(g + j < g1 ? g + j : g) * SA, a[j]);
-#pragma unroll
-            for (int l = 0; l < D; ++l) pre[j][l] = base[l];
-        }
-#pragma unroll
-        for (int f = 0; f < FC; ++f)
-            if (f >= nlo && f < ngi) {
-                T x[NG][D];
-#pragma unroll
-                for (int j = 0; j < NG; ++j) load_run<D>(p[f] + a[j][1 + f], x[j]);
-#pragma unroll
-                for (int j = 0; j < NG; ++j)
-#pragma unroll
-                    for (int l = 0; l < D; ++l) pre[j][l] = C::add(pre[j][l], x[j][l], k);
-            }
-        for (int u = 0; u < R0; ++u) {
-#pragma unroll
-            for (int j = 0; j < NG; ++j)
-                if (g + j < g1) row(a[j], pre[j], u);
-        }
-    }
-}
-
 // Fixed domain D, any number of inputs (offsets reread per input).
 template <typename T, int D>
 __device__ __forceinline__ void item_fixed_anyF(const TaskDev &tk, const unsigned char *stage, int lo,
@@ -292,6 +202,135 @@ __device__ __forceinline__ void item_fixed_anyF(const TaskDev &tk, const unsigne
             out[o] = C::store(best);
             tk.arg[o] = static_cast<uint8_t>(bi);
         }
+    }
+}
+
+// One item for a fixed domain D, at most FC inputs (FC = 3 or 7: A rows of
+// FC + 1 ints, one or two 16-byte loads) of which NR are per-row inputs
+// (they mention the fastest hi digit u).  Lo-only inputs are summed once per
+// item, group inputs once per group (NG groups at a time, so that NG
+// independent loads of the large input are in flight per thread), and each
+// row adds its NR runs, takes the min and first argmin over x_i and writes
+// both.  Row offsets advance by the stride of u: a row costs NR vector
+// loads, the adds, the argmin and two stores.
+template <typename T, int D, int FC, int NR>
+__device__ __forceinline__ void item_fixed_nr(const TaskDev &tk, const unsigned char *stage, int lo, int g0,
+                                              int g1, uint32_t k)
+{
+    using C = Cost<T>;
+    using A = typename C::acc;
+    constexpr int SA = FC + 1;
+    constexpr int SB = (FC + 3) / 4 * 4;
+    constexpr int NG = (FC <= 3 && D <= 4) ? 2 : 1;
+    constexpr int R = NR > 0 ? NR : 1;
+    const int F = tk.F, nlo = tk.n_lo, ngi = tk.n_gi, R0 = tk.R0;
+    const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * SB;
+    // lo-only inputs: summed once
+    A base[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) base[l] = A(0);
+    for (int f = 0; f < nlo; ++f) {
+        T v[D];
+        load_run<D>(input_base<T>(tk.in[f], stage) + Brow[f], v);
+#pragma unroll
+        for (int l = 0; l < D; ++l) base[l] = C::add(base[l], v[l], k);
+    }
+    // group inputs [nlo, ngi) and per-row inputs [ngi, F)
+    const T *gp[FC];
+#pragma unroll
+    for (int f = 0; f < FC; ++f)
+        gp[f] = (f >= nlo && f < ngi) ? input_base<T>(tk.in[f], stage) + Brow[f] : nullptr;
+    const T *rp[R];
+    int32_t dr[R];
+    const int32_t *du = tk.A + static_cast<int64_t>(tk.G) * SA;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        rp[r] = input_base<T>(tk.in[ngi + r], stage) + Brow[ngi + r];
+        dr[r] = du[1 + ngi + r];
+    }
+    const int32_t d0 = du[0];
+    T *out = static_cast<T *>(tk.out);
+    uint8_t *arg = tk.arg;
+    for (int g = g0; g < g1; g += NG) {
+        A pre[NG][D];
+        int32_t ro[NG][R], oo[NG];
+        {
+            int32_t a[NG][SA];
+#pragma unroll
+            for (int j = 0; j < NG; ++j) {
+                load_ints<SA>(tk.A + static_cast<int64_t>(g + j < g1 ? g + j : g) * SA, a[j]);
+#pragma unroll
+                for (int l = 0; l < D; ++l) pre[j][l] = base[l];
+            }
+            // all group-input loads of the NG groups first, then the sums
+#pragma unroll
+            for (int f = 0; f < FC; ++f)
+                if (f >= nlo && f < ngi) {
+                    T x[NG][D];
+#pragma unroll
+                    for (int j = 0; j < NG; ++j) load_run<D>(gp[f] + a[j][1 + f], x[j]);
+#pragma unroll
+                    for (int j = 0; j < NG; ++j)
+#pragma unroll
+                        for (int l = 0; l < D; ++l) pre[j][l] = C::add(pre[j][l], x[j][l], k);
+                }
+#pragma unroll
+            for (int j = 0; j < NG; ++j) {
+                oo[j] = a[j][0] + lo;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    ro[j][r] = 0;
+#pragma unroll
+                    for (int f = 0; f < FC; ++f)
+                        if (f == ngi + r) ro[j][r] = a[j][1 + f];
+                }
+            }
+        }
+        const int nj = (g + 1 < g1) ? NG : 1;
+        for (int u = 0; u < R0; ++u) {
+#pragma unroll
+            for (int j = 0; j < NG; ++j) {
+                if (j < nj) {
+                    A acc[D];
+#pragma unroll
+                    for (int l = 0; l < D; ++l) acc[l] = pre[j][l];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        T v[D];
+                        load_run<D>(rp[r] + ro[j][r], v);
+                        ro[j][r] += dr[r];
+#pragma unroll
+                        for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
+                    }
+                    A best = acc[0];
+                    int bi = 0;
+#pragma unroll
+                    for (int l = 1; l < D; ++l)
+                        if (acc[l] < best) {
+                            best = acc[l];
+                            bi = l;
+                        }
+                    out[oo[j]] = C::store(best);
+                    arg[oo[j]] = static_cast<uint8_t>(bi);
+                    oo[j] += d0;
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int D, int FC>
+__device__ __forceinline__ void item_fixed(const TaskDev &tk, const unsigned char *stage, int lo,
+                                           int g0, int g1, uint32_t k)
+{
+    switch (tk.F - tk.n_gi) {
+    case 0: item_fixed_nr<T, D, FC, 0>(tk, stage, lo, g0, g1, k); break;
+    case 1: item_fixed_nr<T, D, FC, 1>(tk, stage, lo, g0, g1, k); break;
+    case 2: item_fixed_nr<T, D, FC, 2>(tk, stage, lo, g0, g1, k); break;
+    default:
+        if constexpr (FC <= 3) item_fixed_nr<T, D, FC, 3>(tk, stage, lo, g0, g1, k);
+        else item_fixed_anyF<T, D>(tk, stage, lo, g0, g1, k);
+        break;
     }
 }
 
