@@ -272,6 +272,42 @@ def bucket_case(args):
     return 0
 
 
+def grid_rows_case(args, rows=3):
+    """BE on the first `rows` rows of the headline grid (same tables, natural
+    order, every bucket of row 1 is a full 4^13-entry bucket), a few GB on
+    the device: the case for kernel profiles of full-size launches."""
+    import torch
+    import synth
+    import paper_1608_05288_gb300 as gb
+    from paper_1608_05288_gb300 import _build
+    _build.build()
+    inst = synth.config_instance(1, 0)
+    nv = 12 * rows
+    keep = [j for j, s in enumerate(inst.scopes) if int(np.max(s)) < nv]
+    sub = synth.Instance("grid12x12_rows", inst.dom[:nv].copy(), [inst.scopes[j] for j in keep],
+                         [inst.tables[j] for j in keep], "int", inst.top_k)
+    kw = {}
+    if args.threads:
+        kw["block_threads"] = args.threads
+    if args.rows:
+        kw["rows_per_item"] = args.rows
+    st = gb.UtilState(sub, "be", order="natural", use_graph=True, **kw)
+    st.bind()
+    info = st.info()
+    ms = []
+    for k in range(args.warmup + args.steps):
+        st.run()
+        st.sync()
+        if k >= args.warmup:
+            ms.append(st.times()[0])
+    m = statistics.median(ms)
+    peak, kind = _peaks()
+    print(json.dumps({"case": f"grid12x{rows}", "util_ms": m, "alg_bytes": info["alg_bytes"],
+                      "gbs": info["alg_bytes"] / m / 1e6, "frac": info["alg_bytes"] / m / 1e6 / peak,
+                      "launches": info["n_levels"], "arena_gb": info["arena_bytes"] / 1e9}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -279,12 +315,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-secondary", action="store_true")
-    ap.add_argument("--case", default="", choices=["", "bucket13"])
+    ap.add_argument("--case", default="", choices=["", "bucket13", "grid3"])
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--rows", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
     if args.case == "bucket13":
         return bucket_case(args)
+    if args.case == "grid3":
+        return grid_rows_case(args, 3)
 
     import torch
     import torch.distributed as dist

@@ -33,7 +33,8 @@ def _cuda_include():
 
 
 def _headers():
-    return (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    return (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+            + glob.glob(os.path.join(ROOT, "include", "*.h"))
             + [os.path.join(CSRC, "exports.map")])
 
 

@@ -469,6 +469,15 @@ static int build_descriptors(util_state *s)
         x.stage_bytes = T.stage_bytes;
         x.n_lo = T.n_lo;
         x.n_gi = T.n_gi;
+        // one global group input, at most 3 inputs, a fixed-domain variant:
+        // prefetch that input with the per-thread cp.async pipeline
+        x.pipe = (x.F <= 3 && T.d >= 2 && T.d <= 8 && T.n_gi - T.n_lo == 1 && T.stage_off[T.n_lo] < 0 &&
+                  T.G > 1)
+                     ? 1
+                     : 0;
+        x.n_uo = T.n_uo;
+        // a row of the cp.async path sums 2 + (F - n_uo) terms, each <= top_k
+        x.lazy = (static_cast<uint64_t>(2 + x.F - T.n_uo) * w.top_k <= 0xFFFFFFFFull) ? 1 : 0;
         for (size_t f = 0; f < T.inputs.size(); ++f) {
             InDev &in = ind[in_pos + f];
             in.ptr = func_ptr(s, T.inputs[f]);
@@ -499,12 +508,36 @@ static int build_descriptors(util_state *s)
         L.tasks = td_dev + first;
         L.prefix = pre_dev + pp;
         L.n_tasks = count;
-        int64_t tot = 0;
-        int smem = 0;
+        int smem = 0, pipe_d = 0;
+        double work = 0.0;  // thread-rows of the launch, idle lanes of partial lo chunks included
         for (int i = 0; i < count; ++i) {
+            const TaskDev &x = td[first + i];
+            smem = std::max(smem, x.stage_bytes);
+            if (x.pipe) pipe_d = std::max(pipe_d, x.d);
+            work += static_cast<double>(x.nlc) * NT * x.G * x.R0;
+        }
+        // shared memory: staged tables | the item's A rows | pipeline slots
+        // and four per-u partial sums per thread (cp.async path)
+        L.arows_off = static_cast<int32_t>(al(smem, 16));
+        L.pipe_off = L.arows_off + (pipe_d ? kMaxPipeRows * 16 : 0);
+        if (pipe_d) smem = L.pipe_off + kPipe * NT * pipe_d * 4 + 4 * NT * pipe_d * 4;
+        const int64_t cap = static_cast<int64_t>(blocks_per_sm(smem)) * s->num_sms;
+        // whole waves: items of about equal size, about a multiple of the
+        // resident CTAs, near rows_per_item rows per thread
+        const double pref = std::max(s->cfg.rows_per_item, 1);
+        const double waves = std::max(1.0, std::round(work / (static_cast<double>(cap) * NT * pref)));
+        const double rows_per_thread = work / (waves * cap * NT);
+        int64_t tot = 0;
+        for (int i = 0; i < count; ++i) {
+            TaskDev &x = td[first + i];
+            const int64_t hc = std::llround(rows_per_thread / std::max(x.R0, 1));
+            x.hc = static_cast<int32_t>(std::min<int64_t>(std::max<int64_t>(hc, 1), x.G));
+            if (x.pipe) x.hc = std::min(x.hc, kMaxPipeRows);  // its A rows fit the shared-memory area
+            const int64_t items = static_cast<int64_t>(x.nlc) * ((x.G + x.hc - 1) / x.hc);
+            if (items > INT32_MAX / 2) return set_error(GPUBE_ENOMEM, "a task has too many work items");
+            x.n_items = static_cast<int32_t>(items);
             pre[pp + i] = static_cast<int32_t>(tot);
-            tot += td[first + i].n_items;
-            smem = std::max(smem, td[first + i].stage_bytes);
+            tot += items;
         }
         pre[pp + count] = static_cast<int32_t>(tot);
         pp += count + 1;
@@ -513,7 +546,6 @@ static int build_descriptors(util_state *s)
         L.counter = counters + counter_idx;
         L.status = status;
         L.top_k = w.top_k;
-        const int64_t cap = static_cast<int64_t>(blocks_per_sm(smem)) * s->num_sms;
         s->launches.push_back(L);
         s->launch_grid.push_back(static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(tot, cap))));
         s->launch_smem.push_back(smem);
@@ -868,7 +900,7 @@ extern "C" int util_autotune(util_state *s, int32_t *threads, int32_t *rows_per_
             }
     }
     const int cand_t[] = {128, 256, 512};
-    const int cand_r[] = {2, 4, 8, 16, 32, 64};
+    const int cand_r[] = {16, 32, 64, 128, 256};
     LaunchCfg best = s->cfg;
     double best_ms = 1e30;
     for (int th : cand_t)

@@ -59,8 +59,17 @@ struct alignas(16) TaskDev {
     int32_t n_lo;              // inputs [0, n_lo) depend on lo only
     int32_t n_gi;              // inputs [n_lo, n_gi) do not depend on u
     int32_t R0;                // radix of u (1 when there is no hi digit)
-    int32_t pad0, pad1;
+    int32_t pipe;              // 1: the one group input is prefetched by cp.async
+    int32_t n_uo;              // inputs [n_gi, n_uo) mention no hi digit but u
+    int32_t lazy;              // 1: a row's sum of 2 + (F - n_uo) terms cannot wrap in uint32
+    int32_t pad0, pad1, pad2;
 };
+
+// Depth of the per-thread cp.async pipeline of group inputs (groups ahead),
+// and the most groups one item of that path spans (its A rows are copied to
+// shared memory, 16 bytes each).
+constexpr int kPipe = 4;
+constexpr int kMaxPipeRows = 256;
 
 // One kernel launch: a list of tasks whose work items are handed out by an
 // atomic counter (a device-side work queue).
@@ -72,6 +81,8 @@ struct LaunchDev {
     int32_t *counter;       // queue head, zeroed before the launch
     int32_t *status;        // error word (kStatus*)
     uint32_t top_k;         // WCSP saturation value
+    int32_t pipe_off;       // byte offset of the cp.async pipeline area in shared memory
+    int32_t arows_off;      // byte offset of the item's A rows (cp.async path) in shared memory
     int32_t pad;
 };
 

@@ -65,6 +65,7 @@ struct Task {
     int64_t G = 1;                 // groups = H / R0
     int32_t R0 = 1;                // radix of the fastest hi digit
     int32_t n_gi = 0;              // inputs [n_lo, n_gi) do not mention the fastest hi digit
+    int32_t n_uo = 0;              // inputs [n_gi, n_uo) mention no other hi digit
     int32_t sa = 4, sb = 4;
     int32_t n_lo = 0;              // leading inputs that depend on lo digits only
     std::vector<int32_t> hperm;    // hi digit indices, fastest first
@@ -97,7 +98,7 @@ struct Plan {
 // Launch parameters of one run.
 struct LaunchCfg {
     int32_t threads = 256;
-    int32_t rows_per_item = 32;
+    int32_t rows_per_item = 128;
 };
 
 // planner (plan.cpp)

@@ -493,22 +493,25 @@ void shape_tasks(const wcsp &w, Plan &P)
         T.hperm.insert(T.hperm.end(), present.begin(), present.end());
         T.R0 = T.hperm.empty() ? 1 : w.dom[T.sep[T.hperm[0]]];
         T.G = T.H / T.R0;
-        // inputs: lo digits only | hi digits but not u | u
+        // inputs: lo digits only | hi digits but not u | u as the only hi digit | u and others
         {
-            std::vector<int32_t> lo_only, group, row;
+            std::vector<int32_t> lo_only, group, u_only, row;
             for (int fid : T.inputs) {
                 const auto &fs = P.funcs[fid].scope;
                 auto has = [&](int j) { return std::find(fs.begin(), fs.end(), T.sep[j]) != fs.end(); };
-                bool hi = false;
-                for (int j = 0; j < m - T.L && !hi; ++j) hi = has(j);
-                if (!hi) lo_only.push_back(fid);
+                int nhi = 0;
+                for (int j = 0; j < m - T.L; ++j) nhi += has(j);
+                if (nhi == 0) lo_only.push_back(fid);
                 else if (!has(T.hperm[0])) group.push_back(fid);
+                else if (nhi == 1) u_only.push_back(fid);
                 else row.push_back(fid);
             }
             T.n_lo = static_cast<int32_t>(lo_only.size());
             T.n_gi = static_cast<int32_t>(lo_only.size() + group.size());
+            T.n_uo = static_cast<int32_t>(T.n_gi + u_only.size());
             T.inputs = lo_only;
             T.inputs.insert(T.inputs.end(), group.begin(), group.end());
+            T.inputs.insert(T.inputs.end(), u_only.begin(), u_only.end());
             T.inputs.insert(T.inputs.end(), row.begin(), row.end());
         }
         T.sa = arow_of(F);

@@ -278,7 +278,7 @@ extern "C" int srv_step(gpube_server *s)
     // merge the next level of every running request into one launch
     std::vector<TaskDev> tds;
     std::vector<Request *> finishing;
-    int smem = 0;
+    int smem = 0, pipe_d = 0;
     for (Request *r : s->active) {
         if (r->state != kActive) continue;
         if (!r->up_waited) {
@@ -292,6 +292,7 @@ extern "C" int srv_step(gpube_server *s)
             for (int i = P.level_off[r->next_level]; i < P.level_off[r->next_level + 1]; ++i) {
                 tds.push_back(td[i]);
                 smem = std::max(smem, td[i].stage_bytes);
+                if (td[i].pipe) pipe_d = std::max(pipe_d, td[i].d);
             }
             r->next_level++;
         }
@@ -329,6 +330,9 @@ extern "C" int srv_step(gpube_server *s)
         L.counter = s->work + b;
         L.status = s->work + 2;
         L.top_k = s->active.front()->st->w->top_k;
+        L.arows_off = static_cast<int32_t>(al(smem, 16));
+        L.pipe_off = L.arows_off + (pipe_d ? kMaxPipeRows * 16 : 0);
+        if (pipe_d) smem = L.pipe_off + kPipe * s->threads * pipe_d * 4 + 4 * s->threads * pipe_d * 4;
         SRV_TRY(cudaMemsetAsync(L.counter, 0, 4, s->stream));
         const int cost_type = s->active.front()->st->w->cost_type;
         const int64_t cap = static_cast<int64_t>(util_max_blocks_per_sm(cost_type, s->threads, smem)) * s->num_sms;

@@ -1,0 +1,901 @@
+// UTIL and VALUE kernel templates for sm_103a; instantiated per cost type in
+// util_kernel_i32.cu and util_kernel_f32.cu.
+#pragma once
+// UTIL-table kernels for sm_103a.
+//
+// One kernel computes every bucket function of Algorithms 1-2 (and DPOP's
+// UTIL messages): for each separator row r and each value l of the
+// eliminated variable x_i it gathers one entry of every input table, sums
+// them (saturating at the top cost for integer WCSPs, Section 2; fp32 for
+// -log p costs, Section 3), and keeps the minimum and first argmin over l.
+// This fuses the paper's Gpu::Aggregate (Eq. 3 gather, Section 6.3) and
+// Gpu::Eliminate (Section 6.4): no joint table is materialised, every input
+// entry is read where it is needed, the output is written once.
+//
+// Index arithmetic.  Rows are split r = hi * P_lo + lo (lo = the lowest
+// separator digits).  A thread keeps its lo fixed and walks a range of hi
+// values; the per-input offsets of Eq. 3 are read from two small tables
+// (A[hi][f] uniform across the CTA, B[lo][f] once per thread), so the hot
+// loop has no division or modulo.  The order in which hi is walked is the
+// planner's choice (digits absent from the largest input first), which makes
+// consecutive steps of a thread reread the same input rows from L1 instead
+// of DRAM.
+//
+// Small input tables are staged in shared memory by TMA bulk copies
+// (cp.async.bulk, completion on an mbarrier); their x_i-runs are then read
+// with vector loads.  Work items (one lo chunk of blockDim.x rows times a
+// range of hi values) are taken from an atomic counter, so one launch can
+// serve one bucket (the per-bucket form) or every bucket of an
+// elimination-tree level (the batched form).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "gpube_dev.h"
+
+namespace gpube {
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on the staging barrier; false when the limit was reached.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (int i = 0; i < kMaxSpin; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Per-thread asynchronous global -> shared copies (completion tracked per
+// thread by commit / wait groups).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src)
+{
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES)
+                     : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// ------------------------------------------------------------ cost ops
+template <typename T> struct Cost;
+
+// Integer WCSP costs in [0, k]: sums saturate at k (k means "not allowed").
+// Both operands are <= k < 2^31, so their uint32 sum cannot wrap.
+template <> struct Cost<int32_t> {
+    using acc = uint32_t;
+    static __device__ __forceinline__ acc from(int32_t v) { return static_cast<uint32_t>(v); }
+    static __device__ __forceinline__ acc add(acc a, int32_t v, uint32_t k)
+    {
+        uint32_t s = a + static_cast<uint32_t>(v);
+        return s < k ? s : k;
+    }
+    static __device__ __forceinline__ int32_t store(acc a) { return static_cast<int32_t>(a); }
+};
+
+// -log p costs in fp32; +inf (p = 0) propagates through the sum.
+template <> struct Cost<float> {
+    using acc = float;
+    static __device__ __forceinline__ acc from(float v) { return v; }
+    static __device__ __forceinline__ acc add(acc a, float v, uint32_t) { return a + v; }
+    static __device__ __forceinline__ float store(acc a) { return a; }
+};
+
+template <typename T> using A_t = typename Cost<T>::acc;
+
+// The d entries of one x_i-run, loaded with the widest aligned vector:
+// offsets are multiples of d, so d % 4 == 0 runs are 16-byte aligned.
+template <int D, typename T>
+__device__ __forceinline__ void load_run(const T *p, T (&v)[D])
+{
+    if constexpr (D % 4 == 0) {
+        using V4 = typename std::conditional<std::is_same<T, float>::value, float4, int4>::type;
+#pragma unroll
+        for (int i = 0; i < D / 4; ++i) {
+            V4 x = reinterpret_cast<const V4 *>(p)[i];
+            v[4 * i + 0] = x.x;
+            v[4 * i + 1] = x.y;
+            v[4 * i + 2] = x.z;
+            v[4 * i + 3] = x.w;
+        }
+    } else if constexpr (D % 2 == 0) {
+        using V2 = typename std::conditional<std::is_same<T, float>::value, float2, int2>::type;
+#pragma unroll
+        for (int i = 0; i < D / 2; ++i) {
+            V2 x = reinterpret_cast<const V2 *>(p)[i];
+            v[2 * i + 0] = x.x;
+            v[2 * i + 1] = x.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) v[i] = p[i];
+    }
+}
+
+// A thread's run of D values stored in shared memory as D*4/CH chunks of CH
+// bytes laid out [chunk][thread] (chunk c of thread t at base + (c*NT + t)*CH):
+// one vector access per chunk keeps a warp's accesses conflict-free.
+template <int D, int CH, typename V>
+__device__ __forceinline__ void slot_load(const unsigned char *base, int NT, int tid, V (&v)[D])
+{
+    static_assert(sizeof(V) == 4, "4-byte values");
+#pragma unroll
+    for (int c = 0; c < D * 4 / CH; ++c) {
+        const unsigned char *q = base + (static_cast<size_t>(c) * NT + tid) * CH;
+        if constexpr (CH == 16) {
+            const uint4 x = *reinterpret_cast<const uint4 *>(q);
+            v[4 * c + 0] = __builtin_bit_cast(V, x.x);
+            v[4 * c + 1] = __builtin_bit_cast(V, x.y);
+            v[4 * c + 2] = __builtin_bit_cast(V, x.z);
+            v[4 * c + 3] = __builtin_bit_cast(V, x.w);
+        } else if constexpr (CH == 8) {
+            const uint2 x = *reinterpret_cast<const uint2 *>(q);
+            v[2 * c + 0] = __builtin_bit_cast(V, x.x);
+            v[2 * c + 1] = __builtin_bit_cast(V, x.y);
+        } else {
+            v[c] = *reinterpret_cast<const V *>(q);
+        }
+    }
+}
+
+template <int D, int CH, typename V>
+__device__ __forceinline__ void slot_store(unsigned char *base, int NT, int tid, const V (&v)[D])
+{
+#pragma unroll
+    for (int c = 0; c < D * 4 / CH; ++c) {
+        unsigned char *q = base + (static_cast<size_t>(c) * NT + tid) * CH;
+        if constexpr (CH == 16) {
+            *reinterpret_cast<uint4 *>(q) =
+                make_uint4(__builtin_bit_cast(uint32_t, v[4 * c]), __builtin_bit_cast(uint32_t, v[4 * c + 1]),
+                           __builtin_bit_cast(uint32_t, v[4 * c + 2]), __builtin_bit_cast(uint32_t, v[4 * c + 3]));
+        } else if constexpr (CH == 8) {
+            *reinterpret_cast<uint2 *>(q) =
+                make_uint2(__builtin_bit_cast(uint32_t, v[2 * c]), __builtin_bit_cast(uint32_t, v[2 * c + 1]));
+        } else {
+            *reinterpret_cast<V *>(q) = v[c];
+        }
+    }
+}
+
+// Base pointer of input f: its shared-memory copy when staged.
+template <typename T>
+__device__ __forceinline__ const T *input_base(const InDev &in, const unsigned char *stage)
+{
+    return in.stage_off >= 0 ? reinterpret_cast<const T *>(stage + in.stage_off)
+                             : reinterpret_cast<const T *>(in.ptr);
+}
+
+// --------------------------------------------------------- item bodies
+template <int N>
+__device__ __forceinline__ void load_ints(const int32_t *p, int32_t (&a)[N])
+{
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+        const int4 x = reinterpret_cast<const int4 *>(p)[i];
+        a[4 * i + 0] = x.x;
+        a[4 * i + 1] = x.y;
+        a[4 * i + 2] = x.z;
+        a[4 * i + 3] = x.w;
+    }
+}
+
+// Fixed domain D, any number of inputs (offsets reread per input).
+template <typename T, int D>
+__device__ __noinline__ void item_fixed_anyF(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo,
+                                                int g0, int g1, uint32_t k)
+{
+    const TaskDev tk = *tkp;
+    using C = Cost<T>;
+    using A = typename C::acc;
+    const int F = tk.F;
+    const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * tk.sb;
+    const int32_t *du = tk.A + static_cast<int64_t>(tk.G) * tk.sa;
+    T *out = static_cast<T *>(tk.out);
+    for (int g = g0; g < g1; ++g) {
+        const int32_t *Ar = tk.A + static_cast<int64_t>(g) * tk.sa;
+        for (int u = 0; u < tk.R0; ++u) {
+            A acc[D];
+#pragma unroll
+            for (int l = 0; l < D; ++l) acc[l] = A(0);
+            for (int f = 0; f < F; ++f) {
+                T v[D];
+                load_run<D>(input_base<T>(tk.in[f], stage) + (Ar[1 + f] + u * du[1 + f] + Brow[f]), v);
+#pragma unroll
+                for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
+            }
+            A best = acc[0];
+            int bi = 0;
+#pragma unroll
+            for (int l = 1; l < D; ++l)
+                if (acc[l] < best) {
+                    best = acc[l];
+                    bi = l;
+                }
+            const int o = Ar[0] + u * du[0] + lo;
+            out[o] = C::store(best);
+            tk.arg[o] = static_cast<uint8_t>(bi);
+        }
+    }
+}
+
+// One item for a fixed domain D, at most FC inputs (FC = 3 or 7: A rows of
+// FC + 1 ints, one or two 16-byte loads) of which NR are per-row inputs
+// (they mention the fastest hi digit u).  Lo-only inputs are summed once per
+// item, group inputs once per group (NG groups at a time, so that NG
+// independent loads of the large input are in flight per thread), and each
+// row adds its NR runs, takes the min and first argmin over x_i and writes
+// both.  Row offsets advance by the stride of u: a row costs NR vector
+// loads, the adds, the argmin and two stores.
+template <typename T, int D, int FC, int NR>
+__device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo, int g0,
+                                              int g1, uint32_t k)
+{
+    const TaskDev tk = *tkp;
+    using C = Cost<T>;
+    using A = typename C::acc;
+    constexpr int SA = FC + 1;
+    constexpr int SB = (FC + 3) / 4 * 4;
+    constexpr int NG = (FC <= 3 && D <= 4) ? 2 : 1;
+    constexpr int R = NR > 0 ? NR : 1;
+    const int F = tk.F, nlo = tk.n_lo, ngi = tk.n_gi, R0 = tk.R0;
+    const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * SB;
+    // lo-only inputs: summed once
+    A base[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) base[l] = A(0);
+    for (int f = 0; f < nlo; ++f) {
+        T v[D];
+        load_run<D>(input_base<T>(tk.in[f], stage) + Brow[f], v);
+#pragma unroll
+        for (int l = 0; l < D; ++l) base[l] = C::add(base[l], v[l], k);
+    }
+    // group inputs [nlo, ngi) and per-row inputs [ngi, F)
+    const T *gp[FC];
+#pragma unroll
+    for (int f = 0; f < FC; ++f)
+        gp[f] = (f >= nlo && f < ngi) ? input_base<T>(tk.in[f], stage) + Brow[f] : nullptr;
+    const T *rp[R];
+    int32_t dr[R];
+    const int32_t *du = tk.A + static_cast<int64_t>(tk.G) * SA;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        rp[r] = input_base<T>(tk.in[ngi + r], stage) + Brow[ngi + r];
+        dr[r] = du[1 + ngi + r];
+    }
+    const int32_t d0 = du[0];
+    T *out = static_cast<T *>(tk.out);
+    uint8_t *arg = tk.arg;
+    for (int g = g0; g < g1; g += NG) {
+        A pre[NG][D];
+        int32_t ro[NG][R], oo[NG];
+        {
+            int32_t a[NG][SA];
+#pragma unroll
+            for (int j = 0; j < NG; ++j) {
+                load_ints<SA>(tk.A + static_cast<int64_t>(g + j < g1 ? g + j : g) * SA, a[j]);
+#pragma unroll
+                for (int l = 0; l < D; ++l) pre[j][l] = base[l];
+            }
+            // all group-input loads of the NG groups first, then the sums
+#pragma unroll
+            for (int f = 0; f < FC; ++f)
+                if (f >= nlo && f < ngi) {
+                    T x[NG][D];
+#pragma unroll
+                    for (int j = 0; j < NG; ++j) load_run<D>(gp[f] + a[j][1 + f], x[j]);
+#pragma unroll
+                    for (int j = 0; j < NG; ++j)
+#pragma unroll
+                        for (int l = 0; l < D; ++l) pre[j][l] = C::add(pre[j][l], x[j][l], k);
+                }
+#pragma unroll
+            for (int j = 0; j < NG; ++j) {
+                oo[j] = a[j][0] + lo;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    ro[j][r] = 0;
+#pragma unroll
+                    for (int f = 0; f < FC; ++f)
+                        if (f == ngi + r) ro[j][r] = a[j][1 + f];
+                }
+            }
+        }
+        const int nj = (g + 1 < g1) ? NG : 1;
+        for (int u = 0; u < R0; ++u) {
+#pragma unroll
+            for (int j = 0; j < NG; ++j) {
+                if (j < nj) {
+                    A acc[D];
+#pragma unroll
+                    for (int l = 0; l < D; ++l) acc[l] = pre[j][l];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        T v[D];
+                        load_run<D>(rp[r] + ro[j][r], v);
+                        ro[j][r] += dr[r];
+#pragma unroll
+                        for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
+                    }
+                    A best = acc[0];
+                    int bi = 0;
+#pragma unroll
+                    for (int l = 1; l < D; ++l)
+                        if (acc[l] < best) {
+                            best = acc[l];
+                            bi = l;
+                        }
+                    out[oo[j]] = C::store(best);
+                    arg[oo[j]] = static_cast<uint8_t>(bi);
+                    oo[j] += d0;
+                }
+            }
+        }
+    }
+}
+
+// Same item, when exactly one input is a group input and lives in global
+// memory (the usual large child bucket function): its run for group g + kPipe
+// is copied to this thread's shared-memory slot by cp.async while group g is
+// processed, so kPipe loads per thread are in flight without holding
+// registers.  Slot layout [slot][chunk][thread] keeps the reads conflict-free.
+//
+// FOLD (R0 <= 4): the inputs whose only hi digit is u are added, once per
+// item, into one partial sum per value of u, so such rows need no load.
+// NRG counts the remaining per-row inputs.  With no per-row input a row sums
+// two terms (partial sum + group run, each <= k, no uint32 wrap), so the
+// saturation is applied once, after the min: if the minimum reaches k every
+// clamped entry equals k and the first argmin is 0.
+template <typename T, int D, int NRG, bool FOLD>
+__device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const unsigned char *stage, unsigned char *pipe,
+                                          const int32_t *arows, int lo, int g0, int g1, uint32_t k)
+{
+    const TaskDev tk = *tkp;
+    using C = Cost<T>;
+    using A = typename C::acc;
+    constexpr bool kInt = std::is_same<T, int32_t>::value;
+    constexpr int FC = 3, SA = 4, SB = 4, UMAX = 4;
+    constexpr int R = NRG > 0 ? NRG : 1;
+    constexpr int CH = (D % 4 == 0) ? 16 : (D % 2 == 0) ? 8 : 4;  // bytes per copy
+    constexpr int NCH = D * 4 / CH;                                  // copies per run
+    const int NT = blockDim.x, tid = threadIdx.x;
+    const int nlo = tk.n_lo, ngi = tk.n_gi, R0 = tk.R0;
+    const int rg0 = FOLD ? tk.n_uo : ngi;  // first general per-row input
+    const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * SB;
+    const int32_t *du = tk.A + static_cast<int64_t>(tk.G) * SA;
+    A base[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) base[l] = A(0);
+    for (int f = 0; f < nlo; ++f) {
+        T v[D];
+        load_run<D>(input_base<T>(tk.in[f], stage) + Brow[f], v);
+#pragma unroll
+        for (int l = 0; l < D; ++l) base[l] = C::add(base[l], v[l], k);
+    }
+    // shared-memory areas of this thread: the pipeline slots (group runs),
+    // the slots' A rows, and the per-u partial sums, each laid out
+    // [index][chunk][thread] so that the 16-byte reads are conflict-free
+    unsigned char *bus = pipe + static_cast<size_t>(kPipe) * NCH * NT * CH;
+    if constexpr (FOLD) {
+        for (int u = 0; u < R0; ++u) {
+            A bu[D];
+#pragma unroll
+            for (int l = 0; l < D; ++l) bu[l] = base[l];
+            for (int f = ngi; f < tk.n_uo; ++f) {
+                T v[D];
+                load_run<D>(input_base<T>(tk.in[f], stage) + (Brow[f] + u * du[1 + f]), v);
+#pragma unroll
+                for (int l = 0; l < D; ++l) bu[l] = C::add(bu[l], v[l], k);
+            }
+            slot_store<D, CH>(bus + static_cast<size_t>(u) * NCH * NT * CH, NT, tid, bu);
+        }
+    }
+    const int gf = nlo;  // the group input
+    const T *gp = reinterpret_cast<const T *>(tk.in[gf].ptr) + Brow[gf];
+    const T *rp[R];
+    int32_t dr[R];
+#pragma unroll
+    for (int r = 0; r < NRG; ++r) {
+        rp[r] = input_base<T>(tk.in[rg0 + r], stage) + Brow[rg0 + r];
+        dr[r] = du[1 + rg0 + r];
+    }
+    const int32_t d0 = du[0];
+    T *out = static_cast<T *>(tk.out);
+    uint8_t *arg = tk.arg;
+    // the item's A rows are in shared memory (arows[(g - g0) * SA + slot]);
+    // each pipeline slot holds, per thread, one group run
+    auto issue = [&](int g, int slot) {
+        if (g < g1) {
+            const T *src = gp + arows[(g - g0) * SA + 1 + gf];
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+                cp_async<CH>(pipe + (static_cast<size_t>(slot * NCH + c) * NT + tid) * CH,
+                             reinterpret_cast<const unsigned char *>(src) + c * CH);
+        }
+        cp_async_commit();
+    };
+    // one output row: b (partial sum) + x (group run) + the NRG per-row runs
+    auto row = [&](const A (&b)[D], const T (&x)[D], int32_t (&ro)[R], int32_t o) {
+        A acc[D];
+        if constexpr (NRG == 0 && kInt) {
+#pragma unroll
+            for (int l = 0; l < D; ++l) acc[l] = b[l] + static_cast<A>(x[l]);  // <= 2k, no wrap
+        } else {
+#pragma unroll
+            for (int l = 0; l < D; ++l) acc[l] = C::add(b[l], x[l], k);
+#pragma unroll
+            for (int r = 0; r < NRG; ++r) {
+                T v[D];
+                load_run<D>(rp[r] + ro[r], v);
+                ro[r] += dr[r];
+#pragma unroll
+                for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
+            }
+        }
+        A best = acc[0];
+        int bi = 0;
+#pragma unroll
+        for (int l = 1; l < D; ++l)
+            if (acc[l] < best) {
+                best = acc[l];
+                bi = l;
+            }
+        if constexpr (NRG == 0 && kInt) {
+            if (best >= k) {
+                best = k;
+                bi = 0;
+            }
+        }
+        out[o] = C::store(best);
+        arg[o] = static_cast<uint8_t>(bi);
+    };
+#pragma unroll
+    for (int s = 0; s < kPipe; ++s) issue(g0 + s, s);
+    int slot = 0;
+    for (int g = g0; g < g1; ++g) {
+        cp_async_wait<kPipe - 1>();
+        int32_t a[SA];
+        load_ints<SA>(arows + (g - g0) * SA, a);
+        T x[D];
+        slot_load<D, CH>(pipe + static_cast<size_t>(slot) * NCH * NT * CH, NT, tid, x);
+        int32_t ro[R];
+#pragma unroll
+        for (int r = 0; r < NRG; ++r) {
+            ro[r] = 0;
+#pragma unroll
+            for (int f = 0; f < FC; ++f)
+                if (f == rg0 + r) ro[r] = a[1 + f];
+        }
+        int32_t o = a[0] + lo;
+        if constexpr (FOLD) {
+#pragma unroll
+            for (int u = 0; u < UMAX; ++u)
+                if (u < R0) {
+                    A bu[D];
+                    slot_load<D, CH>(bus + static_cast<size_t>(u) * NCH * NT * CH, NT, tid, bu);
+                    row(bu, x, ro, o);
+                    o += d0;
+                }
+            issue(g + kPipe, slot);  // the slot's data has been consumed
+        } else {
+            A pre[D];
+#pragma unroll
+            for (int l = 0; l < D; ++l) pre[l] = C::add(base[l], x[l], k);
+            issue(g + kPipe, slot);
+            T zero[D];
+#pragma unroll
+            for (int l = 0; l < D; ++l) zero[l] = T(0);
+            for (int u = 0; u < R0; ++u) {
+                row(pre, zero, ro, o);
+                o += d0;
+            }
+        }
+        slot = (slot + 1 == kPipe) ? 0 : slot + 1;
+    }
+    cp_async_wait<0>();
+}
+
+template <typename T, int D, int FC>
+__device__ __forceinline__ void item_fixed(const TaskDev *__restrict__ tkp, const TaskDev &tk,
+                                           const unsigned char *stage, unsigned char *pipe, const int32_t *arows,
+                                           int lo, int g0, int g1, uint32_t k)
+{
+    if constexpr (FC <= 3) {
+        if (tk.pipe) {
+            if (tk.R0 <= 4) {
+                switch (tk.F - tk.n_uo) {
+                case 0: item_pipe<T, D, 0, true>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                case 1: item_pipe<T, D, 1, true>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                default: item_pipe<T, D, 2, true>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                }
+            } else {
+                switch (tk.F - tk.n_gi) {
+                case 0: item_pipe<T, D, 0, false>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                case 1: item_pipe<T, D, 1, false>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                default: item_pipe<T, D, 2, false>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                }
+            }
+            return;
+        }
+    }
+    switch (tk.F - tk.n_gi) {
+    case 0: item_fixed_nr<T, D, FC, 0>(tkp, stage, lo, g0, g1, k); break;
+    case 1: item_fixed_nr<T, D, FC, 1>(tkp, stage, lo, g0, g1, k); break;
+    case 2: item_fixed_nr<T, D, FC, 2>(tkp, stage, lo, g0, g1, k); break;
+    default:
+        if constexpr (FC <= 3) item_fixed_nr<T, D, FC, 3>(tkp, stage, lo, g0, g1, k);
+        else item_fixed_anyF<T, D>(tkp, stage, lo, g0, g1, k);
+        break;
+    }
+}
+
+// Any domain size (runtime loop over x_i's values), at most FC inputs.
+template <typename T, int FC>
+__device__ __noinline__ void item_anyD(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo, int g0,
+                                          int g1, uint32_t k)
+{
+    const TaskDev tk = *tkp;
+    using C = Cost<T>;
+    using A = typename C::acc;
+    constexpr int SA = FC + 1;
+    constexpr int SB = (FC + 3) / 4 * 4;
+    const int F = tk.F, d = tk.d;
+    int32_t b[SB];
+    load_ints<SB>(tk.B + static_cast<int64_t>(lo) * SB, b);
+    int32_t du[SA];
+    load_ints<SA>(tk.A + static_cast<int64_t>(tk.G) * SA, du);
+    const T *p[FC];
+#pragma unroll
+    for (int f = 0; f < FC; ++f) p[f] = (f < F) ? input_base<T>(tk.in[f], stage) + b[f] : nullptr;
+    T *out = static_cast<T *>(tk.out);
+    for (int g = g0; g < g1; ++g) {
+        int32_t a[SA];
+        load_ints<SA>(tk.A + static_cast<int64_t>(g) * SA, a);
+        for (int u = 0; u < tk.R0; ++u) {
+            const T *q[FC];
+#pragma unroll
+            for (int f = 0; f < FC; ++f) q[f] = (f < F) ? p[f] + (a[1 + f] + u * du[1 + f]) : nullptr;
+            A best = A(0);
+            int bi = 0;
+            for (int l = 0; l < d; ++l) {
+                A s = C::from(q[0][l]);
+#pragma unroll
+                for (int f = 1; f < FC; ++f)
+                    if (f < F) s = C::add(s, q[f][l], k);
+                if (l == 0 || s < best) {
+                    best = s;
+                    bi = l;
+                }
+            }
+            const int o = a[0] + u * du[0] + lo;
+            out[o] = C::store(best);
+            tk.arg[o] = static_cast<uint8_t>(bi);
+        }
+    }
+}
+
+// Any domain size, any number of inputs.
+template <typename T>
+__device__ __noinline__ void item_anyD_anyF(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo,
+                                               int g0, int g1, uint32_t k)
+{
+    const TaskDev tk = *tkp;
+    using C = Cost<T>;
+    using A = typename C::acc;
+    const int F = tk.F, d = tk.d;
+    const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * tk.sb;
+    const int32_t *du = tk.A + static_cast<int64_t>(tk.G) * tk.sa;
+    T *out = static_cast<T *>(tk.out);
+    for (int g = g0; g < g1; ++g) {
+        const int32_t *Ar = tk.A + static_cast<int64_t>(g) * tk.sa;
+        for (int u = 0; u < tk.R0; ++u) {
+            A best = A(0);
+            int bi = 0;
+            for (int l = 0; l < d; ++l) {
+                A s = A(0);
+                for (int f = 0; f < F; ++f)
+                    s = C::add(s, input_base<T>(tk.in[f], stage)[Ar[1 + f] + u * du[1 + f] + Brow[f] + l], k);
+                if (l == 0 || s < best) {
+                    best = s;
+                    bi = l;
+                }
+            }
+            const int o = Ar[0] + u * du[0] + lo;
+            out[o] = C::store(best);
+            tk.arg[o] = static_cast<uint8_t>(bi);
+        }
+    }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void dispatch_f(const TaskDev *__restrict__ tkp, const TaskDev &tk, int fc,
+                                           const unsigned char *stage, unsigned char *pipe, const int32_t *arows,
+                                           int lo, int h0, int h1, uint32_t k)
+{
+    if constexpr (D == 0) {
+        switch (fc) {
+        case 0: item_anyD<T, 3>(tkp, stage, lo, h0, h1, k); break;
+        case 1: item_anyD<T, 7>(tkp, stage, lo, h0, h1, k); break;
+        default: item_anyD_anyF<T>(tkp, stage, lo, h0, h1, k); break;
+        }
+    } else {
+        switch (fc) {
+        case 0: item_fixed<T, D, 3>(tkp, tk, stage, pipe, arows, lo, h0, h1, k); break;
+        case 1: item_fixed<T, D, 7>(tkp, tk, stage, pipe, arows, lo, h0, h1, k); break;
+        default: item_fixed_anyF<T, D>(tkp, stage, lo, h0, h1, k); break;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void dispatch(const TaskDev *__restrict__ tkp, const TaskDev &tk,
+                                         const unsigned char *stage, unsigned char *pipe, const int32_t *arows,
+                                         int lo, int h0, int h1, uint32_t k)
+{
+    const int dc = tk.variant / kNumFClass, fc = tk.variant % kNumFClass;
+    switch (dc) {
+    case 1: dispatch_f<T, 2>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 2: dispatch_f<T, 3>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 3: dispatch_f<T, 4>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 4: dispatch_f<T, 5>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 5: dispatch_f<T, 6>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 6: dispatch_f<T, 7>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 7: dispatch_f<T, 8>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    default: dispatch_f<T, 0>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    }
+}
+
+// ------------------------------------------------------------- kernel
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
+{
+    extern __shared__ __align__(128) unsigned char stage[];
+    __shared__ uint64_t bar;
+    __shared__ int s_item[2];
+    __shared__ int s_staged;  // task whose tables are in shared memory, -1 = none
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        s_staged = -1;
+        s_item[0] = atomicAdd(L.counter, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    int it = 0;
+    int item = s_item[0];
+    while (item < L.total_items) {
+        const int nb = (it + 1) & 1;
+        if (tid == 0) s_item[nb] = atomicAdd(L.counter, 1);  // prefetch the next item
+
+        // task of this item: last t with prefix[t] <= item
+        int a = 0, b = L.n_tasks;
+        while (b - a > 1) {
+            const int mid = (a + b) >> 1;
+            if (L.prefix[mid] <= item) a = mid;
+            else b = mid;
+        }
+        const TaskDev tk = L.tasks[a];
+
+        const int local = item - L.prefix[a];
+        const int hr = local / tk.nlc;
+        const int lc = local - hr * tk.nlc;
+        const int h0 = hr * tk.hc;
+        const int h1 = min(h0 + tk.hc, tk.G);
+        // one TMA transaction per item: the task's small tables (when this CTA
+        // has not staged them yet) and, for the cp.async path, the item's
+        // contiguous A rows
+        const bool restage = tk.stage_bytes > 0 && s_staged != a;
+        const uint32_t rows_bytes = tk.pipe ? static_cast<uint32_t>(h1 - h0) * 16u : 0u;
+        if (restage || rows_bytes) {
+            __syncthreads();  // every thread is done with the previous copies
+            if (tid == 0) {
+                fence_proxy_async();
+                mbar_arrive_expect_tx(&bar, (restage ? static_cast<uint32_t>(tk.stage_bytes) : 0u) + rows_bytes);
+                if (restage) {
+                    for (int f = 0; f < tk.F; ++f) {
+                        const InDev in = tk.in[f];
+                        if (in.stage_off >= 0)
+                            tma_bulk_g2s(stage + in.stage_off, in.ptr, static_cast<uint32_t>(in.bytes16), &bar);
+                    }
+                    s_staged = a;
+                }
+                if (rows_bytes) tma_bulk_g2s(stage + L.arows_off, tk.A + static_cast<int64_t>(h0) * 4, rows_bytes, &bar);
+            }
+            bool ok = mbar_wait_bounded(&bar, phase);
+            if (__syncthreads_or(!ok)) {
+                // give up on this launch: flag it, let the copies land (bounded), leave
+                if (tid == 0) atomicExch(L.status, kStatusTimeout);
+                mbar_wait_bounded(&bar, phase);
+                return;
+            }
+            phase ^= 1u;
+        }
+
+        const int lo = lc * blockDim.x + tid;
+        if (lo < tk.P_lo)
+            dispatch<T>(L.tasks + a, tk, stage, stage + L.pipe_off, reinterpret_cast<const int32_t *>(stage + L.arows_off),
+                        lo, h0, h1, L.top_k);
+
+        __syncthreads();
+        item = s_item[nb];
+        ++it;
+    }
+}
+
+// ------------------------------------------------------------- VALUE
+__device__ __forceinline__ long long warp_sum_ll(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Index of a term's table entry under the current assignment (warp-wide).
+__device__ __forceinline__ long long term_index(const ValueDev &V, const ValueTerm &t,
+                                                const unsigned char *sig, int lane)
+{
+    long long idx = 0;
+    for (int j = lane; j < t.nv; j += 32)
+        idx += static_cast<long long>(sig[V.vvars[t.var_off + j]]) * V.vstrides[t.var_off + j];
+    return warp_sum_ll(idx);
+}
+
+// VALUE phase in one CTA: variables grouped by dependency level (a variable
+// depends on the other variables of its bucket, all eliminated later), one
+// warp per variable.  BE / DPOP read the stored argmin of the bucket
+// function at the separator's assignment; MBE takes the first argmin of the
+// sum of every function of the bucket.  Then the root constants are summed
+// (the optimum or lower bound) and the Eq. 1 cost of the assignment is
+// evaluated over the original functions.
+template <typename T>
+__global__ void __launch_bounds__(256) value_kernel(const ValueDev V)
+{
+    using C = Cost<T>;
+    using A = typename C::acc;
+    extern __shared__ unsigned char sig[];
+    __shared__ double red[2][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int v = threadIdx.x; v < V.n; v += blockDim.x) sig[v] = 0;
+    __syncthreads();
+    for (int lev = 0; lev < V.n_levels; ++lev) {
+        const int b = V.lev_off[lev], e = V.lev_off[lev + 1];
+        for (int i = b + warp; i < e; i += nw) {
+            const int v = V.vorder[i];
+            const ValueVar vi = V.vinfo[v];
+            int val = 0;
+            if (vi.mode == 1) {
+                const ValueTerm t = V.terms[vi.term_off];
+                const long long idx = term_index(V, t, sig, lane);
+                val = static_cast<const uint8_t *>(t.tab)[idx];
+            } else if (vi.mode == 2) {
+                constexpr int kMaxRuns = 8;  // domains up to 256 values
+                A acc[kMaxRuns];
+                for (int term = 0; term < vi.n_terms; ++term) {
+                    const ValueTerm t = V.terms[vi.term_off + term];
+                    const long long base = term_index(V, t, sig, lane);
+                    const T *tab = static_cast<const T *>(t.tab) + base;
+#pragma unroll
+                    for (int r = 0; r < kMaxRuns; ++r) {
+                        const int l = lane + 32 * r;
+                        if (l < vi.d) acc[r] = term == 0 ? C::from(tab[l]) : C::add(acc[r], tab[l], V.top_k);
+                    }
+                }
+                // first argmin over l: per lane, then across the warp
+                A best = A(0);
+                int bl = -1;
+#pragma unroll
+                for (int r = 0; r < kMaxRuns; ++r) {
+                    const int l = lane + 32 * r;
+                    if (l < vi.d && (bl < 0 || acc[r] < best)) {
+                        best = acc[r];
+                        bl = l;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const A ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+                    if (ol >= 0 && (bl < 0 || ob < best || (!(best < ob) && ol < bl))) {
+                        best = ob;
+                        bl = ol;
+                    }
+                }
+                val = bl < 0 ? 0 : bl;
+            }
+            if (lane == 0) sig[v] = static_cast<unsigned char>(val);
+        }
+        __syncthreads();
+    }
+    // Eq. 1 cost of the assignment and the sum of the root constants
+    double c = 0.0, rb = 0.0;
+    for (int i = threadIdx.x; i < V.n_evals; i += blockDim.x) {
+        const ValueTerm t = V.evals[i];
+        long long idx = 0;
+        for (int j = 0; j < t.nv; ++j)
+            idx += static_cast<long long>(sig[V.vvars[t.var_off + j]]) * V.vstrides[t.var_off + j];
+        c += static_cast<double>(static_cast<const T *>(t.tab)[idx]);
+    }
+    for (int i = threadIdx.x; i < V.n_roots; i += blockDim.x)
+        rb += static_cast<double>(static_cast<const T *>(V.roots[i])[0]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        rb += __shfl_xor_sync(0xffffffffu, rb, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = c;
+        red[1][warp] = rb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tc = V.const_sum, tb = V.const_sum;
+        for (int w = 0; w < nw; ++w) {
+            tc += red[0][w];
+            tb += red[1][w];
+        }
+        if (!V.is_float) {
+            const double k = static_cast<double>(V.top_k);
+            tc = tc > k ? k : tc;
+            tb = tb > k ? k : tb;
+        }
+        V.result[0] = tb;
+        V.result[1] = tc;
+    }
+    for (int v = threadIdx.x; v < V.n; v += blockDim.x) V.sigma[v] = sig[v];
+}
+
+}  // namespace gpube
