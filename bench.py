@@ -37,6 +37,8 @@ METRIC = "UTIL entries/s"
 UNIT = "entries/s"
 WORKLOAD = "BE 12x12 grid WCSP, d=4, int32 U[0,1000], natural order (w*=12, max table 4^13)"
 L2_FLUSH_BYTES = 512 << 20
+# tuned launch shapes (CTA size, rows per item) per plan, kept beside the build
+TUNE_CACHE = os.path.join(ROOT, "paper_1608_05288_gb300", "_build", "autotune.txt")
 
 
 def _peaks():
@@ -346,8 +348,9 @@ def main():
     dev = torch.device(f"cuda:{local}")
 
     inst = synth.config_instance(1, seed=rank)  # one replica per rank
-    st = gb.UtilState(inst, "be", order="best", use_graph=True, device=local)
+    st = gb.UtilState(inst, "be", order="best", use_graph=True, device=local, autotune_cache=TUNE_CACHE)
     st.bind(device=local)
+    threads, rows = st.autotune()  # launch shape measured on this instance (cached)
     info = st.info()
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -412,7 +415,7 @@ def main():
         t0 = time.perf_counter()
         w = gb.WCSP(inst)
         r = gb.be_solve(w, order="best", arena=arena.data_ptr(), arena_bytes=arena.numel(),
-                        stream=stream.cuda_stream, device=local)
+                        stream=stream.cuda_stream, device=local, block_threads=threads, rows_per_item=rows)
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_s.append(t1 - t0)
@@ -444,6 +447,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "buckets": info["n_tasks"], "levels": info["n_levels"],
+                           "block_threads": threads, "rows_per_item": rows,
                            "util_entries_per_step": info["util_entries"],
                            "l2": "flushed between steps (512 MB write)",
                            "parallelism": f"replicas x{world}", "bound": res.bound},

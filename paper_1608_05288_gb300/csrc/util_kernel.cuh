@@ -166,48 +166,84 @@ __device__ __forceinline__ void load_run(const T *p, T (&v)[D])
 }
 
 // A thread's run of D values stored in shared memory as D*4/CH chunks of CH
-// bytes laid out [chunk][thread] (chunk c of thread t at base + (c*NT + t)*CH):
-// one vector access per chunk keeps a warp's accesses conflict-free.
+// bytes laid out [chunk][thread] (chunk c of thread t at base + (c*NT + t)*CH,
+// base a 32-bit shared-window address): one vector access per chunk keeps a
+// warp's accesses conflict-free.
 template <int D, int CH, typename V>
-__device__ __forceinline__ void slot_load(const unsigned char *base, int NT, int tid, V (&v)[D])
+__device__ __forceinline__ void slot_load(uint32_t base, int NT, int tid, V (&v)[D])
 {
     static_assert(sizeof(V) == 4, "4-byte values");
 #pragma unroll
     for (int c = 0; c < D * 4 / CH; ++c) {
-        const unsigned char *q = base + (static_cast<size_t>(c) * NT + tid) * CH;
+        const uint32_t q = base + static_cast<uint32_t>((c * NT + tid) * CH);
         if constexpr (CH == 16) {
-            const uint4 x = *reinterpret_cast<const uint4 *>(q);
-            v[4 * c + 0] = __builtin_bit_cast(V, x.x);
-            v[4 * c + 1] = __builtin_bit_cast(V, x.y);
-            v[4 * c + 2] = __builtin_bit_cast(V, x.z);
-            v[4 * c + 3] = __builtin_bit_cast(V, x.w);
+            uint32_t x0, x1, x2, x3;
+            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(x0), "=r"(x1), "=r"(x2), "=r"(x3)
+                         : "r"(q)
+                         : "memory");
+            v[4 * c + 0] = __builtin_bit_cast(V, x0);
+            v[4 * c + 1] = __builtin_bit_cast(V, x1);
+            v[4 * c + 2] = __builtin_bit_cast(V, x2);
+            v[4 * c + 3] = __builtin_bit_cast(V, x3);
         } else if constexpr (CH == 8) {
-            const uint2 x = *reinterpret_cast<const uint2 *>(q);
-            v[2 * c + 0] = __builtin_bit_cast(V, x.x);
-            v[2 * c + 1] = __builtin_bit_cast(V, x.y);
+            uint32_t x0, x1;
+            asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(x0), "=r"(x1) : "r"(q) : "memory");
+            v[2 * c + 0] = __builtin_bit_cast(V, x0);
+            v[2 * c + 1] = __builtin_bit_cast(V, x1);
         } else {
-            v[c] = *reinterpret_cast<const V *>(q);
+            uint32_t x0;
+            asm volatile("ld.shared.b32 %0, [%1];" : "=r"(x0) : "r"(q) : "memory");
+            v[c] = __builtin_bit_cast(V, x0);
         }
     }
 }
 
 template <int D, int CH, typename V>
-__device__ __forceinline__ void slot_store(unsigned char *base, int NT, int tid, const V (&v)[D])
+__device__ __forceinline__ void slot_store(uint32_t base, int NT, int tid, const V (&v)[D])
 {
 #pragma unroll
     for (int c = 0; c < D * 4 / CH; ++c) {
-        unsigned char *q = base + (static_cast<size_t>(c) * NT + tid) * CH;
+        const uint32_t q = base + static_cast<uint32_t>((c * NT + tid) * CH);
         if constexpr (CH == 16) {
-            *reinterpret_cast<uint4 *>(q) =
-                make_uint4(__builtin_bit_cast(uint32_t, v[4 * c]), __builtin_bit_cast(uint32_t, v[4 * c + 1]),
-                           __builtin_bit_cast(uint32_t, v[4 * c + 2]), __builtin_bit_cast(uint32_t, v[4 * c + 3]));
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(q), "r"(__builtin_bit_cast(uint32_t, v[4 * c])),
+                         "r"(__builtin_bit_cast(uint32_t, v[4 * c + 1])), "r"(__builtin_bit_cast(uint32_t, v[4 * c + 2])),
+                         "r"(__builtin_bit_cast(uint32_t, v[4 * c + 3]))
+                         : "memory");
         } else if constexpr (CH == 8) {
-            *reinterpret_cast<uint2 *>(q) =
-                make_uint2(__builtin_bit_cast(uint32_t, v[2 * c]), __builtin_bit_cast(uint32_t, v[2 * c + 1]));
+            asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(q), "r"(__builtin_bit_cast(uint32_t, v[2 * c])),
+                         "r"(__builtin_bit_cast(uint32_t, v[2 * c + 1]))
+                         : "memory");
         } else {
-            *reinterpret_cast<V *>(q) = v[c];
+            asm volatile("st.shared.b32 [%0], %1;" ::"r"(q), "r"(__builtin_bit_cast(uint32_t, v[c])) : "memory");
         }
     }
+}
+
+// Four ints from a 32-bit shared-window address (a uniform A row).
+__device__ __forceinline__ void lds_int4(uint32_t q, int32_t (&a)[4])
+{
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                 : "r"(q)
+                 : "memory");
+}
+
+__device__ __forceinline__ int32_t lds_int(uint32_t q)
+{
+    int32_t x;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(x) : "r"(q) : "memory");
+    return x;
+}
+
+// Asynchronous copy into a 32-bit shared-window address.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_s(uint32_t dst, const void *src)
+{
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(BYTES) : "memory");
 }
 
 // Base pointer of input f: its shared-memory copy when staged.
@@ -427,7 +463,9 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     // shared-memory areas of this thread: the pipeline slots (group runs),
     // the slots' A rows, and the per-u partial sums, each laid out
     // [index][chunk][thread] so that the 16-byte reads are conflict-free
-    unsigned char *bus = pipe + static_cast<size_t>(kPipe) * NCH * NT * CH;
+    const uint32_t pipe_s = smem_addr(pipe);
+    const uint32_t bus_s = pipe_s + static_cast<uint32_t>(kPipe * NCH * NT * CH);
+    const uint32_t arows_s = smem_addr(arows);
     if constexpr (FOLD) {
         for (int u = 0; u < R0; ++u) {
             A bu[D];
@@ -439,7 +477,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
 #pragma unroll
                 for (int l = 0; l < D; ++l) bu[l] = C::add(bu[l], v[l], k);
             }
-            slot_store<D, CH>(bus + static_cast<size_t>(u) * NCH * NT * CH, NT, tid, bu);
+            slot_store<D, CH>(bus_s + static_cast<uint32_t>(u * NCH * NT * CH), NT, tid, bu);
         }
     }
     const int gf = nlo;  // the group input
@@ -458,11 +496,11 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     // each pipeline slot holds, per thread, one group run
     auto issue = [&](int g, int slot) {
         if (g < g1) {
-            const T *src = gp + arows[(g - g0) * SA + 1 + gf];
+            const T *src = gp + lds_int(arows_s + static_cast<uint32_t>(((g - g0) * SA + 1 + gf) * 4));
 #pragma unroll
             for (int c = 0; c < NCH; ++c)
-                cp_async<CH>(pipe + (static_cast<size_t>(slot * NCH + c) * NT + tid) * CH,
-                             reinterpret_cast<const unsigned char *>(src) + c * CH);
+                cp_async_s<CH>(pipe_s + static_cast<uint32_t>(((slot * NCH + c) * NT + tid) * CH),
+                               reinterpret_cast<const unsigned char *>(src) + c * CH);
         }
         cp_async_commit();
     };
@@ -507,9 +545,9 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     for (int g = g0; g < g1; ++g) {
         cp_async_wait<kPipe - 1>();
         int32_t a[SA];
-        load_ints<SA>(arows + (g - g0) * SA, a);
+        lds_int4(arows_s + static_cast<uint32_t>((g - g0) * SA * 4), a);
         T x[D];
-        slot_load<D, CH>(pipe + static_cast<size_t>(slot) * NCH * NT * CH, NT, tid, x);
+        slot_load<D, CH>(pipe_s + static_cast<uint32_t>(slot * NCH * NT * CH), NT, tid, x);
         int32_t ro[R];
 #pragma unroll
         for (int r = 0; r < NRG; ++r) {
@@ -524,7 +562,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
             for (int u = 0; u < UMAX; ++u)
                 if (u < R0) {
                     A bu[D];
-                    slot_load<D, CH>(bus + static_cast<size_t>(u) * NCH * NT * CH, NT, tid, bu);
+                    slot_load<D, CH>(bus_s + static_cast<uint32_t>(u * NCH * NT * CH), NT, tid, bu);
                     row(bu, x, ro, o);
                     o += d0;
                 }
