@@ -248,7 +248,7 @@ static void build_value_plan(const wcsp &w, Plan &P)
 
 // Arena layout: originals | bucket functions | argmins | A/B tables |
 // descriptors | value plan | counters, status, result, assignment.
-static void layout(util_state *s)
+void gpube_layout(util_state *s)
 {
     const wcsp &w = *s->w;
     Plan &P = s->plan;
@@ -257,12 +257,13 @@ static void layout(util_state *s)
         if (!P.funcs[j].scope.empty() && !P.funcs[j].ext) P.funcs[j].off = c.take(P.funcs[j].size * 4, 16);
     c.off = al(c.off, 256);
     s->upload_bytes = c.off;
+    // (tables the caller owns, single-bucket calls, take no arena space)
     for (size_t t = 0; t < P.tasks.size(); ++t) {
         Task &T = P.tasks[t];
-        T.out_off = c.take(T.rows * 4, 128);
+        T.out_off = T.ext_out ? 0 : c.take(T.rows * 4, 128);
         P.funcs[w.nf + t].off = T.out_off;
     }
-    for (Task &T : P.tasks) T.arg_off = c.take(T.rows, 128);
+    for (Task &T : P.tasks) T.arg_off = T.ext_arg ? 0 : c.take(T.rows, 128);
     for (Task &T : P.tasks) {
         T.A_off = c.take(static_cast<size_t>(T.G + 1) * T.sa * 4, 128);
         T.B_off = c.take(static_cast<size_t>(T.P_lo) * T.sb * 4, 128);
@@ -358,7 +359,7 @@ extern "C" int util_plan(wcsp *w, int32_t kind, int32_t i_bound, const int32_t *
         return rc;
     }
     shape_tasks(*w, s->plan);
-    layout(s);
+    gpube_layout(s);
     if (w->n > 200 * 1024) {
         delete s;
         return set_error(GPUBE_EINVAL, "more than 204800 variables are not supported by the VALUE kernel");
@@ -424,7 +425,7 @@ static const void *func_ptr(const util_state *s, int fid)
 // Rebuild the launch-configuration-dependent descriptors (TaskDev, InDev,
 // work-item prefixes) and the static ones (expansion plan, value plan) into
 // the host blob that mirrors [desc_off, value_off + value_bytes).
-static int build_descriptors(util_state *s)
+int gpube_build_descriptors(util_state *s)
 {
     const wcsp &w = *s->w;
     Plan &P = s->plan;
@@ -644,7 +645,7 @@ static void drop_graph(util_state *s)
 
 static int upload_descriptors(util_state *s)
 {
-    int rc = build_descriptors(s);
+    int rc = gpube_build_descriptors(s);
     if (rc) return rc;
     drop_graph(s);
     CUDA_TRY(cudaMemcpyAsync(s->base + s->desc_off, s->host_blob.data(), s->host_blob.size(),
@@ -731,7 +732,7 @@ extern "C" int util_bind(util_state *s, void *arena, size_t arena_bytes, void *s
     return GPUBE_OK;
 }
 
-static int enqueue_util(util_state *s, cudaStream_t st)
+int gpube_enqueue_util(util_state *s, cudaStream_t st)
 {
     const size_t n_counters = std::max<size_t>(s->launches.size(), 1);
     CUDA_TRY(cudaMemsetAsync(s->base + s->counters_off, 0, 4 * n_counters, st));
@@ -748,7 +749,7 @@ extern "C" int util_run(util_state *s)
         if (!s->graph) {
             cudaGraph_t g = nullptr;
             CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-            int rc = enqueue_util(s, s->cap_stream);
+            int rc = gpube_enqueue_util(s, s->cap_stream);
             cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
             if (rc) {
                 if (g) cudaGraphDestroy(g);
@@ -764,7 +765,7 @@ extern "C" int util_run(util_state *s)
         CUDA_TRY(cudaEventRecord(s->ev[1], s->stream));
     } else {
         CUDA_TRY(cudaEventRecord(s->ev[0], s->stream));
-        int rc = enqueue_util(s, s->stream);
+        int rc = gpube_enqueue_util(s, s->stream);
         if (rc) return rc;
         CUDA_TRY(cudaEventRecord(s->ev[1], s->stream));
     }
@@ -1065,7 +1066,7 @@ extern "C" int util_bucket(int32_t cost_type, int32_t top_k, int32_t m, const in
     P.level_order = {0};
     P.level_off = {0, 1};
     shape_tasks(w, P);
-    layout(&s);
+    gpube_layout(&s);
     s.batched = false;
     s.use_graph = false;
     int dev = 0;
@@ -1091,7 +1092,7 @@ extern "C" int util_bucket(int32_t cost_type, int32_t top_k, int32_t m, const in
         sc.bytes = s.arena_bytes;
     }
     s.base = static_cast<unsigned char *>(sc.p);
-    int rc = build_descriptors(&s);
+    int rc = gpube_build_descriptors(&s);
     if (!rc) {
         const DescLayout &D = layout_of(&s);
         cudaError_t e = cudaMemcpyAsync(s.base + s.desc_off, s.host_blob.data(), s.host_blob.size(),
@@ -1103,7 +1104,7 @@ extern "C" int util_bucket(int32_t cost_type, int32_t top_k, int32_t m, const in
                               P.tasks[0].G + 1 + P.tasks[0].P_lo, reinterpret_cast<const int32_t *>(s.base + D.pool),
                               s.num_sms, s.stream);
         if (e != cudaSuccess) rc = cuda_error(e, "util_bucket upload");
-        else rc = enqueue_util(&s, s.stream);
+        else rc = gpube_enqueue_util(&s, s.stream);
     }
     return rc;
 }

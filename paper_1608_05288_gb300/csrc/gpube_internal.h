@@ -167,3 +167,9 @@ struct util_state {
     std::vector<unsigned char> host_blob;  // staging for uploads
     DescLayout dl;
 };
+
+// api.cpp: arena layout of a planned state, its device descriptors (into
+// host_blob), and the UTIL launches of one run on a stream.
+void gpube_layout(util_state *s);
+int gpube_build_descriptors(util_state *s);
+int gpube_enqueue_util(util_state *s, cudaStream_t st);
