@@ -258,6 +258,25 @@ int util_bucket(int32_t cost_type, int32_t top_k, int32_t m, const int32_t *sep_
                 int32_t n_in, const void *const *in_tables, const int32_t *in_pos_off,
                 const int32_t *in_pos, void *out, uint8_t *arg, void *stream);
 
+/* The same single-bucket computation for callers that must not allocate
+ * device memory: code running while a CUDA graph is being captured, loops
+ * that forbid allocation after start-up, processes whose device memory is
+ * owned by another allocator.  The paper has no counterpart; it is a service
+ * of this library.  Its scratch (offset tables, descriptors, work counter) is
+ * a fixed 4 MiB array inside the library, present on every device the
+ * library is used on from load until process exit; nothing is allocated and
+ * nothing is freed.  Arguments as util_bucket.  Buckets whose scratch would
+ * exceed the array fail with GPUBE_ENOMEM before any GPU work (util_bucket
+ * takes them).  The first call on a device, with that device current, looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (each call clears its counter and status first): calls
+ * that may overlap on the GPU (different streams, or threads) race and must
+ * be serialised by the caller.  Asynchronous on stream. */
+int util_bucket_noalloc(int32_t cost_type, int32_t top_k, int32_t m, const int32_t *sep_dom, int32_t d,
+                        int32_t n_in, const void *const *in_tables, const int32_t *in_pos_off,
+                        const int32_t *in_pos, void *out, uint8_t *arg, void *stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /* A continuous-batching server for streams of problems (DCOP or WCSP) on one

@@ -78,6 +78,9 @@ SIGNATURES = {
     "util_last_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "util_bucket": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, i32p, C.c_int32, C.c_int32,
                               C.POINTER(C.c_void_p), i32p, i32p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "util_bucket_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, i32p, C.c_int32, C.c_int32,
+                                      C.POINTER(C.c_void_p), i32p, i32p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
     "srv_create": (C.c_int, [C.c_size_t, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
                              C.POINTER(C.c_void_p)]),
     "srv_submit": (C.c_int64, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, i32p,
