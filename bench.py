@@ -50,6 +50,20 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _traffic_per_launch():
+    """DRAM bytes per UTIL launch from the committed ncu capture, or None when
+    the kernel source changed since that capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        src = os.path.join(ROOT, "paper_1608_05288_gb300", "csrc", "util_kernel.cuh")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return t["util_kernel_grid12_bytes_per_launch"] if t.get("source_sha256_16") == h else None
+    except Exception:
+        return None
+
+
 class Clocks:
     """nvidia-smi samples during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -293,8 +307,11 @@ def grid_rows_case(args, rows=3):
         kw["block_threads"] = args.threads
     if args.rows:
         kw["rows_per_item"] = args.rows
-    st = gb.UtilState(sub, "be", order="natural", use_graph=True, **kw)
+    os.makedirs(os.path.dirname(TUNE_CACHE), exist_ok=True)
+    st = gb.UtilState(sub, "be", order="natural", use_graph=True, autotune_cache=TUNE_CACHE, **kw)
     st.bind()
+    if not kw:
+        st.autotune()
     info = st.info()
     ms = []
     for k in range(args.warmup + args.steps):
@@ -317,7 +334,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-secondary", action="store_true")
-    ap.add_argument("--case", default="", choices=["", "bucket13", "grid3"])
+    ap.add_argument("--case", default="", choices=["", "bucket13", "grid3", "grid12"])
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0)
     args = ap.parse_args()
@@ -327,6 +344,8 @@ def main():
         return bucket_case(args)
     if args.case == "grid3":
         return grid_rows_case(args, 3)
+    if args.case == "grid12":
+        return grid_rows_case(args, 12)
 
     import torch
     import torch.distributed as dist
@@ -394,14 +413,10 @@ def main():
     peak, peak_kind = _peaks()
     util_s = sum(util_ms) * 1e-3 / args.steps
     achieved = info["alg_bytes"] / util_s / 1e9
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get("util_kernel_grid12_bytes_per_launch")
-    except Exception:
-        pass
+    traffic = _traffic_per_launch()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                "alg_bytes_per_launch": info["alg_bytes"] / info["n_levels"],
                 "alg_bytes_per_step": info["alg_bytes"], "launches_per_step": info["n_levels"]}
     st.free()
     del flush

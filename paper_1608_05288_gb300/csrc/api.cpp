@@ -694,6 +694,7 @@ extern "C" int util_bind(util_state *s, void *arena, size_t arena_bytes, void *s
         return set_error(GPUBE_ENODEV, "no CUDA device");
     CUDA_TRY(cudaSetDevice(s->device));
     CUDA_TRY(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device));
+    CUDA_TRY(kernels_init_device());
     if (!arena) {
         void *p = nullptr;
         cudaError_t e = cudaMalloc(&p, s->arena_bytes);
@@ -1073,6 +1074,7 @@ extern "C" int util_bucket(int32_t cost_type, int32_t top_k, int32_t m, const in
     CUDA_TRY(cudaGetDevice(&dev));
     s.device = dev;
     CUDA_TRY(cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(kernels_init_device());
     s.stream = static_cast<cudaStream_t>(stream);
     // scratch: everything of the layout except the (external) tables
     std::lock_guard<std::mutex> g(g_scratch_mu);

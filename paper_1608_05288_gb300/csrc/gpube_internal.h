@@ -117,6 +117,7 @@ int util_max_blocks_per_sm(int cost_type, int threads, int smem);
 cudaError_t launch_expand(const ExpandDev *tasks, const int64_t *prefix, int n_tasks, int64_t total,
                           const int32_t *pool, int num_sms, cudaStream_t s);
 cudaError_t launch_value(const ValueDev &V, int cost_type, int smem, cudaStream_t s);
+cudaError_t kernels_init_device();
 
 }  // namespace gpube
 

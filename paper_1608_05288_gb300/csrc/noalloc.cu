@@ -139,6 +139,8 @@ extern "C" int util_bucket_noalloc(int32_t cost_type, int32_t top_k, int32_t m, 
     e = cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_error(e, "cudaDeviceGetAttribute");
     s.stream = static_cast<cudaStream_t>(stream);
+    e = kernels_init_device();
+    if (e != cudaSuccess) return cuda_error(e, "kernel attributes");
     int rc = scratch_address(dev, &s.base);
     if (rc) return rc;
     rc = gpube_build_descriptors(&s);

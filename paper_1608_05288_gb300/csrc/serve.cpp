@@ -134,6 +134,10 @@ extern "C" int srv_create(size_t budget_bytes, int32_t max_slots, void *arena, s
     s->max_slots = max_slots;
     s->stream = static_cast<cudaStream_t>(stream);
     cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaError_t e0 = kernels_init_device(); e0 != cudaSuccess) {
+        delete s;
+        return cuda_error(e0, "kernel attributes");
+    }
     if (arena) {
         if (arena_bytes < budget_bytes || reinterpret_cast<uintptr_t>(arena) % 256) {
             delete s;

@@ -2,6 +2,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "gpube_dev.h"
 
 namespace gpube {
@@ -13,6 +15,8 @@ int util_max_blocks_i32(int threads, int smem);
 int util_max_blocks_f32(int threads, int smem);
 cudaError_t launch_value_i32(const ValueDev &V, int smem, cudaStream_t s);
 cudaError_t launch_value_f32(const ValueDev &V, int smem, cudaStream_t s);
+cudaError_t kernel_attrs_i32(int max_smem);
+cudaError_t kernel_attrs_f32(int max_smem);
 
 // ------------------------------------------------------ plan expansion
 // Fills every task's A and B offset tables from its compact plan: the row h
@@ -97,6 +101,27 @@ cudaError_t launch_expand(const ExpandDev *tasks, const int64_t *prefix, int n_t
 cudaError_t launch_value(const ValueDev &V, int cost_type, int smem, cudaStream_t s)
 {
     return cost_type == 1 ? launch_value_f32(V, smem, s) : launch_value_i32(V, smem, s);
+}
+
+// Once per device (current device): allow every kernel the device's largest
+// dynamic shared-memory size, so that no launch needs an attribute change
+// (in particular none during a stream capture).
+cudaError_t kernels_init_device()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(mu);
+    if (done[dev]) return cudaSuccess;
+    int max_smem = 0;
+    e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = kernel_attrs_i32(max_smem - 1024);
+    if (e == cudaSuccess) e = kernel_attrs_f32(max_smem - 1024);
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
 }
 
 }  // namespace gpube

@@ -5,18 +5,12 @@ namespace gpube {
 
 cudaError_t launch_util_f32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s)
 {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(util_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-    }
     util_kernel<float><<<grid, threads, smem, s>>>(L);
     return cudaGetLastError();
 }
 
 int util_max_blocks_f32(int threads, int smem)
 {
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(util_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, util_kernel<float>, threads, smem) != cudaSuccess) {
         cudaGetLastError();
@@ -27,12 +21,18 @@ int util_max_blocks_f32(int threads, int smem)
 
 cudaError_t launch_value_f32(const ValueDev &V, int smem, cudaStream_t s)
 {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(value_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-    }
     value_kernel<float><<<1, 256, smem, s>>>(V);
     return cudaGetLastError();
+}
+
+// Raise the dynamic shared-memory limit of this type's kernels to the
+// device maximum, once per device, outside any stream capture.
+cudaError_t kernel_attrs_f32(int max_smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(util_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(value_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    return e;
 }
 
 }  // namespace gpube

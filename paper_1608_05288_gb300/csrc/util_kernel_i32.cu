@@ -5,18 +5,12 @@ namespace gpube {
 
 cudaError_t launch_util_i32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s)
 {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(util_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-    }
     util_kernel<int32_t><<<grid, threads, smem, s>>>(L);
     return cudaGetLastError();
 }
 
 int util_max_blocks_i32(int threads, int smem)
 {
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(util_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, util_kernel<int32_t>, threads, smem) != cudaSuccess) {
         cudaGetLastError();
@@ -27,12 +21,18 @@ int util_max_blocks_i32(int threads, int smem)
 
 cudaError_t launch_value_i32(const ValueDev &V, int smem, cudaStream_t s)
 {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(value_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-    }
     value_kernel<int32_t><<<1, 256, smem, s>>>(V);
     return cudaGetLastError();
+}
+
+// Raise the dynamic shared-memory limit of this type's kernels to the
+// device maximum, once per device, outside any stream capture.
+cudaError_t kernel_attrs_i32(int max_smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(util_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(value_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    return e;
 }
 
 }  // namespace gpube
