@@ -50,6 +50,24 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(seconds, device):
+    """The slowest rank's time (every rank gets it); the local time when not
+    distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(seconds)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, world, steps, seconds):
+    """Units processed by all ranks (independent replicas) per second of the
+    slowest rank."""
+    return units_per_rank_step * world * steps / seconds
+
+
 def _traffic_per_launch():
     """DRAM bytes per UTIL launch from the committed ncu capture, or None when
     the kernel source changed since that capture."""
@@ -400,12 +418,8 @@ def main():
     st.sync()
     util_ms = [a.elapsed_time(b) for a, b, _ in ev]
     step_ms = [a.elapsed_time(c) for a, _, c in ev]
-    tot_s = sum(step_ms) * 1e-3
-    if world > 1:
-        t = torch.tensor([tot_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_s = float(t.item())
-    value = info["util_entries"] * world * args.steps / tot_s
+    tot_s = max_over_ranks(sum(step_ms) * 1e-3, dev)
+    value = whole_job_rate(info["util_entries"], world, args.steps, tot_s)
     res = st.value()
     n_launch_step = info["n_levels"] + 1  # one UTIL launch per level + the VALUE kernel
 
@@ -435,13 +449,9 @@ def main():
         if k >= args.warmup:
             e2e_s.append(t1 - t0)
         assert r.bound == res.bound
-    e2e_tot = sum(e2e_s)
-    if world > 1:
-        t = torch.tensor([e2e_tot], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = float(t.item())
+    e2e_tot = max_over_ranks(sum(e2e_s), dev)
     h2d = sum(len(t) for t in inst.tables) * 4
-    e2e = {"value": info["util_entries"] * world * args.steps / e2e_tot, "unit": UNIT,
+    e2e = {"value": whole_job_rate(info["util_entries"], world, args.steps, e2e_tot), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24 + 4 * inst.n,
            "ms_per_step": 1e3 * e2e_tot / args.steps}
     del arena
