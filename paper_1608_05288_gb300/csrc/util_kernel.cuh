@@ -697,6 +697,74 @@ __device__ __noinline__ void item_anyD_anyF(const TaskDev *__restrict__ tkp, con
     }
 }
 
+// Wide domains (d >= 32): a warp computes one output row at a time, lane j
+// holding x_i's values j, j + 32, ...; every input's run is read by one
+// coalesced warp access per 32 values, each lane keeps its first minimum and
+// the warp combines (value, index) pairs by shuffles, ties to the lower index.
+// The warp covers the 32 rows lo0 .. lo0 + 31 of its lanes in turn.
+template <typename T, int FC>
+__device__ __noinline__ void item_wide(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo,
+                                       int g0, int g1, uint32_t k)
+{
+    const TaskDev tk = *tkp;
+    using C = Cost<T>;
+    using A = typename C::acc;
+    constexpr int kRuns = 8;  // 8 x 32 lanes >= 255 values
+    const int lane = threadIdx.x & 31;
+    const int lo0 = lo - lane;
+    const int F = tk.F, d = tk.d, R0 = tk.R0;
+    const int32_t *du = tk.A + static_cast<int64_t>(tk.G) * tk.sa;
+    T *out = static_cast<T *>(tk.out);
+    const T *p[FC > 0 ? FC : 1];
+#pragma unroll
+    for (int f = 0; f < FC; ++f) p[f] = (f < F) ? input_base<T>(tk.in[f], stage) : nullptr;
+    for (int r = 0; r < 32 && lo0 + r < tk.P_lo; ++r) {
+        const int rlo = lo0 + r;
+        const int32_t *Brow = tk.B + static_cast<int64_t>(rlo) * tk.sb;
+        for (int g = g0; g < g1; ++g) {
+            const int32_t *Ar = tk.A + static_cast<int64_t>(g) * tk.sa;
+            for (int u = 0; u < R0; ++u) {
+                A acc[kRuns];
+#pragma unroll
+                for (int j = 0; j < kRuns; ++j) acc[j] = A(0);
+                for (int f = 0; f < F; ++f) {
+                    const T *q = (FC > 0 && f < FC ? p[f] : input_base<T>(tk.in[f], stage)) +
+                                 (Ar[1 + f] + u * du[1 + f] + Brow[f]);
+#pragma unroll
+                    for (int j = 0; j < kRuns; ++j) {
+                        const int l = lane + 32 * j;
+                        if (l < d) acc[j] = C::add(acc[j], q[l], k);
+                    }
+                }
+                A best = A(0);
+                int bi = -1;
+#pragma unroll
+                for (int j = 0; j < kRuns; ++j) {
+                    const int l = lane + 32 * j;
+                    if (l < d && (bi < 0 || acc[j] < best)) {
+                        best = acc[j];
+                        bi = l;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const A ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (oi >= 0 && (bi < 0 || ob < best || (!(best < ob) && oi < bi))) {
+                        best = ob;
+                        bi = oi;
+                    }
+                }
+                if (lane == 0) {
+                    const int o = Ar[0] + u * du[0] + rlo;
+                    out[o] = C::store(best);
+                    tk.arg[o] = static_cast<uint8_t>(bi);
+                }
+            }
+        }
+    }
+}
+
 template <typename T, int D>
 __device__ __forceinline__ void dispatch_f(const TaskDev *__restrict__ tkp, const TaskDev &tk, int fc,
                                            const unsigned char *stage, unsigned char *pipe, const int32_t *arows,
@@ -731,6 +799,11 @@ __device__ __forceinline__ void dispatch(const TaskDev *__restrict__ tkp, const 
     case 5: dispatch_f<T, 6>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     case 6: dispatch_f<T, 7>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     case 7: dispatch_f<T, 8>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case kDClassWide:
+        if (fc == 0) item_wide<T, 3>(tkp, stage, lo, h0, h1, k);
+        else if (fc == 1) item_wide<T, 7>(tkp, stage, lo, h0, h1, k);
+        else item_wide<T, 0>(tkp, stage, lo, h0, h1, k);
+        break;
     default: dispatch_f<T, 0>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     }
 }
@@ -804,7 +877,9 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
         }
 
         const int lo = lc * blockDim.x + tid;
-        if (lo < tk.P_lo)
+        // one thread per row, except the wide variant: whole warps, one row at a time
+        const bool wide = tk.variant / kNumFClass == kDClassWide;
+        if (wide ? (lo & ~31) < tk.P_lo : lo < tk.P_lo)
             dispatch<T>(L.tasks + a, tk, stage, stage + L.pipe_off, reinterpret_cast<const int32_t *>(stage + L.arows_off),
                         lo, h0, h1, L.top_k);
 

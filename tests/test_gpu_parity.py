@@ -278,3 +278,29 @@ def test_util_bucket_entry(orc, seed):
         assert np.array_equal(arg.cpu().numpy(), warg)
     else:
         assert fp_close(out.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("d", [32, 40, 100, 255])
+def test_wide_domains_warp_shuffle(orc, d):
+    # eliminated domains of 32 values and more: a warp per row, shuffle argmin
+    for cost_type in ("int", "real"):
+        inst = synth.random_small(d, n=4, dmin=d, dmax=d, n_funcs=6, max_arity=2, cost_type=cost_type)
+        o, _ = orc.minfill(inst)
+        run = orc.eliminate(inst, o, "be")
+        for shape in (dict(), dict(block_threads=64, lo_target=8, rows_per_item=1)):
+            st, res = run_state(inst, "be", order="given", order_array=o, **shape)
+            check_tables(inst, st, run, exact=(cost_type == "int"))
+            if cost_type == "int":
+                assert res.bound == run.bound and list(res.assignment) == list(run.sigma)
+            else:
+                assert fp_close(res.bound, run.bound)
+
+
+def test_paper_random_network_d100(orc):
+    # the shape of the paper's random networks with d = 100 (Section 8.1, p2 = 0.5)
+    inst = synth.random_network_wcsp(6, 100, 0.3, seed=3)
+    o, _ = orc.minfill(inst)
+    run = orc.eliminate(inst, o, "be")
+    st, res = run_state(inst, "be", order="given", order_array=o)
+    check_tables(inst, st, run)
+    assert res.bound == run.bound == res.cost
