@@ -631,7 +631,13 @@ int gpube_build_descriptors(util_state *s)
     vd.is_float = w.cost_type == WCSP_FP32_LOG;
     vd.result = reinterpret_cast<double *>(B + s->result_off);
     vd.sigma = reinterpret_cast<int32_t *>(B + s->sigma_off);
-    s->value_smem = std::max(w.n, 1);
+    vd.n_terms = static_cast<int32_t>(V.terms.size());
+    vd.n_vv = static_cast<int32_t>(V.vvars.size());
+    vd.smem_sig = static_cast<int32_t>(al(std::max(w.n, 1), 16));
+    const size_t plan_bytes = sizeof(ValueVar) * static_cast<size_t>((w.n + 1) & ~1) + sizeof(ValueTerm) * V.terms.size() +
+                              8 * V.vvars.size();
+    vd.plan_in_smem = (vd.smem_sig + plan_bytes <= 160 * 1024) ? 1 : 0;
+    s->value_smem = vd.smem_sig + (vd.plan_in_smem ? static_cast<int32_t>(plan_bytes) : 0);
     return GPUBE_OK;
 }
 

@@ -132,6 +132,9 @@ struct ValueDev {
     int32_t is_float;
     double *result;             // [2]: bound, cost
     int32_t *sigma;             // [n]
+    int32_t n_terms, n_vv;      // entries of terms and of vvars / vstrides
+    int32_t plan_in_smem;       // 1: vinfo, terms, vvars, vstrides are copied to shared memory
+    int32_t smem_sig;           // bytes reserved for the assignment in shared memory (16-aligned)
 };
 
 }  // namespace gpube

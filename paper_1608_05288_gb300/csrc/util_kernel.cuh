@@ -898,12 +898,12 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
 }
 
 // Index of a term's table entry under the current assignment (warp-wide).
-__device__ __forceinline__ long long term_index(const ValueDev &V, const ValueTerm &t,
+__device__ __forceinline__ long long term_index(const int32_t *vvars, const int32_t *vstrides, const ValueTerm &t,
                                                 const unsigned char *sig, int lane)
 {
     long long idx = 0;
     for (int j = lane; j < t.nv; j += 32)
-        idx += static_cast<long long>(sig[V.vvars[t.var_off + j]]) * V.vstrides[t.var_off + j];
+        idx += static_cast<long long>(sig[vvars[t.var_off + j]]) * vstrides[t.var_off + j];
     return warp_sum_ll(idx);
 }
 
@@ -919,27 +919,49 @@ __global__ void __launch_bounds__(256) value_kernel(const ValueDev V)
 {
     using C = Cost<T>;
     using A = typename C::acc;
-    extern __shared__ unsigned char sig[];
+    extern __shared__ __align__(16) unsigned char vsm[];
     __shared__ double red[2][32];
+    unsigned char *sig = vsm;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int v = threadIdx.x; v < V.n; v += blockDim.x) sig[v] = 0;
+    // the per-variable plan, copied once to shared memory when it fits, so a
+    // dependency level waits on one global load (the table entry) only
+    const ValueVar *vinfo = V.vinfo;
+    const ValueTerm *terms = V.terms;
+    const int32_t *vvars = V.vvars, *vstrides = V.vstrides;
+    if (V.plan_in_smem) {
+        ValueVar *s_vinfo = reinterpret_cast<ValueVar *>(vsm + V.smem_sig);
+        ValueTerm *s_terms = reinterpret_cast<ValueTerm *>(s_vinfo + ((V.n + 1) & ~1));
+        int32_t *s_vvars = reinterpret_cast<int32_t *>(s_terms + V.n_terms);
+        int32_t *s_vstrides = s_vvars + V.n_vv;
+        for (int i = threadIdx.x; i < V.n; i += blockDim.x) s_vinfo[i] = V.vinfo[i];
+        for (int i = threadIdx.x; i < V.n_terms; i += blockDim.x) s_terms[i] = V.terms[i];
+        for (int i = threadIdx.x; i < V.n_vv; i += blockDim.x) {
+            s_vvars[i] = V.vvars[i];
+            s_vstrides[i] = V.vstrides[i];
+        }
+        vinfo = s_vinfo;
+        terms = s_terms;
+        vvars = s_vvars;
+        vstrides = s_vstrides;
+    }
     __syncthreads();
     for (int lev = 0; lev < V.n_levels; ++lev) {
         const int b = V.lev_off[lev], e = V.lev_off[lev + 1];
         for (int i = b + warp; i < e; i += nw) {
             const int v = V.vorder[i];
-            const ValueVar vi = V.vinfo[v];
+            const ValueVar vi = vinfo[v];
             int val = 0;
             if (vi.mode == 1) {
-                const ValueTerm t = V.terms[vi.term_off];
-                const long long idx = term_index(V, t, sig, lane);
+                const ValueTerm t = terms[vi.term_off];
+                const long long idx = term_index(vvars, vstrides, t, sig, lane);
                 val = static_cast<const uint8_t *>(t.tab)[idx];
             } else if (vi.mode == 2) {
                 constexpr int kMaxRuns = 8;  // domains up to 256 values
                 A acc[kMaxRuns];
                 for (int term = 0; term < vi.n_terms; ++term) {
-                    const ValueTerm t = V.terms[vi.term_off + term];
-                    const long long base = term_index(V, t, sig, lane);
+                    const ValueTerm t = terms[vi.term_off + term];
+                    const long long base = term_index(vvars, vstrides, t, sig, lane);
                     const T *tab = static_cast<const T *>(t.tab) + base;
 #pragma unroll
                     for (int r = 0; r < kMaxRuns; ++r) {
