@@ -32,8 +32,30 @@ class _Problem(C.Structure):
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
+        _lib = _configure(C.CDLL(_build.build()))
+    return _lib
+
+
+class use_library:
+    """Context manager: run the oracle functions against another build of
+    oracle.c (used by the tests that plant mistakes in a copy of it)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _lib
+        _lib = _configure(C.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+
+
+def _configure(L):
+    if True:
         P = C.POINTER(_Problem)
         ip = C.POINTER(C.c_int)
         L.orc_eval.argtypes = [P, ip]
@@ -66,8 +88,7 @@ def lib():
         L.orc_run_free.argtypes = [C.c_void_p]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_max_threads.restype = C.c_int
-        _lib = L
-    return _lib
+    return L
 
 
 def _iptr(a):

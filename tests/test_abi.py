@@ -161,3 +161,11 @@ def test_plan_sizes_and_levels():
     assert info["util_entries"] == sum(t["rows"] * 4 for t in tasks)
     assert info["alg_bytes"] == 4 * info["in_entries"] + 5 * info["out_entries"]
     assert info["arena_bytes"] >= 5 * info["out_entries"]
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # without the built CUDA library there is no fallback: every call raises
+    monkeypatch.setattr(_abi, "_lib", None)
+    monkeypatch.setattr(_abi, "LIB_PATH", str(tmp_path / "libgpube.so"))
+    with pytest.raises(RuntimeError):
+        gb.WCSP(synth.paper_example())

@@ -245,6 +245,16 @@ def test_minfill_small_graphs(orc):
     assert w == 2 and int(order[0]) == 0
 
 
+def test_minfill_tie_breaks(orc):
+    # triangle 0-1-2 with a pendant 3 on 0: vertices 1, 2, 3 add no fill edge;
+    # the fewest-neighbours rule picks 3, then the triangle by lowest id
+    inst = synth.Instance("tri", np.full(4, 2, np.int32),
+                          [np.array(p, np.int32) for p in ((0, 1), (1, 2), (0, 2), (0, 3))],
+                          [np.zeros(4, np.int64)] * 4, "int", 1 << 30)
+    order, w = orc.minfill(inst)
+    assert list(order) == [3, 0, 1, 2] and w == 2
+
+
 # ------------------------------------------------------ components (Sec. 6.2)
 def test_components_add_up(orc):
     a = synth.random_small(31, n=5, dmax=3, n_funcs=6, with_constant=False)
