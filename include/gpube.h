@@ -277,6 +277,13 @@ int util_bucket_noalloc(int32_t cost_type, int32_t top_k, int32_t m, const int32
                         int32_t n_in, const void *const *in_tables, const int32_t *in_pos_off,
                         const int32_t *in_pos, void *out, uint8_t *arg, void *stream);
 
+/* Diagnostic: launch one CTA that waits, with the same time-bounded wait the
+ * UTIL kernel uses on its TMA barriers, on a barrier that nothing completes.
+ * Returns GPUBE_ETIMEDOUT after about timeout_ns (the failure path ends in a
+ * status, not a hang or a trap; the context stays usable), GPUBE_ECUDA on a
+ * CUDA error.  Synchronous on stream.  The paper has no counterpart. */
+int util_selftest_wait(uint64_t timeout_ns, void *stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /* A continuous-batching server for streams of problems (DCOP or WCSP) on one

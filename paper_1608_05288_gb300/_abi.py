@@ -81,6 +81,7 @@ SIGNATURES = {
     "util_bucket_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, i32p, C.c_int32, C.c_int32,
                                       C.POINTER(C.c_void_p), i32p, i32p, C.c_void_p, C.c_void_p,
                                       C.c_void_p]),
+    "util_selftest_wait": (C.c_int, [C.c_uint64, C.c_void_p]),
     "srv_create": (C.c_int, [C.c_size_t, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
                              C.POINTER(C.c_void_p)]),
     "srv_submit": (C.c_int64, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, i32p,

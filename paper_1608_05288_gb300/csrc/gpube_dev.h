@@ -9,7 +9,8 @@ namespace gpube {
 // Launch-shape limits of the UTIL kernel.
 constexpr int kMaxThreads = 512;      // CTA size upper bound (launch bounds)
 constexpr int kStageAlign = 16;       // bytes: TMA bulk-copy granularity
-constexpr int kMaxSpin = 1 << 20;     // iteration limit of every device-side wait
+constexpr int kMaxSpin = 1 << 24;     // iteration limit of every device-side wait (backstop)
+constexpr unsigned long long kWaitNs = 1000000000ull;  // time limit of every device-side wait: 1 s
 
 // Device status codes written to the status word.
 constexpr int kStatusOk = 0;

@@ -118,6 +118,7 @@ cudaError_t launch_expand(const ExpandDev *tasks, const int64_t *prefix, int n_t
                           const int32_t *pool, int num_sms, cudaStream_t s);
 cudaError_t launch_value(const ValueDev &V, int cost_type, int smem, cudaStream_t s);
 cudaError_t kernels_init_device();
+cudaError_t launch_selftest_wait(int32_t *status, unsigned long long limit_ns, cudaStream_t s);
 
 }  // namespace gpube
 

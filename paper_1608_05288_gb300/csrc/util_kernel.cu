@@ -76,6 +76,48 @@ __global__ void expand_kernel(const ExpandDev *tasks, const int64_t *prefix, int
     }
 }
 
+// ------------------------------------------------------ wait self-test
+// One CTA waits on an mbarrier that nothing ever arrives at: the bounded wait
+// must give up after limit_ns, record the timeout and return, leaving the
+// context usable.
+__device__ __forceinline__ uint32_t st_smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__global__ void selftest_wait_kernel(int32_t *status, unsigned long long limit_ns)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(st_smem_addr(&bar)), "r"(1) : "memory");
+    __syncthreads();
+    const unsigned long long t0 = [] {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        return t;
+    }();
+    bool ok = false;
+    for (int i = 0; i < kMaxSpin && !ok; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(st_smem_addr(&bar)), "r"(0)
+            : "memory");
+        ok = done != 0;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > limit_ns) break;
+    }
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) *status = kStatusTimeout;
+}
+
+cudaError_t launch_selftest_wait(int32_t *status, unsigned long long limit_ns, cudaStream_t s)
+{
+    selftest_wait_kernel<<<1, 64, 0, s>>>(status, limit_ns);
+    return cudaGetLastError();
+}
+
 // -------------------------------------------------------- host launchers
 cudaError_t launch_util(const LaunchDev &L, int cost_type, int grid, int threads, int smem, cudaStream_t s)
 {

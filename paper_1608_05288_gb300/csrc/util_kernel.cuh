@@ -85,11 +85,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait on the staging barrier; false when the limit was reached.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    for (int i = 0; i < kMaxSpin; ++i)
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase: false once limit_ns has passed (or the
+// iteration backstop is reached) without the phase completing.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitNs)
+{
+    const unsigned long long t0 = global_ns();
+    for (int i = 0; i < kMaxSpin; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
     return false;
 }
 
