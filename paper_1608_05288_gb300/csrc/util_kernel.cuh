@@ -446,7 +446,9 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
 // two terms (partial sum + group run, each <= k, no uint32 wrap), so the
 // saturation is applied once, after the min: if the minimum reaches k every
 // clamped entry equals k and the first argmin is 0.
-template <typename T, int D, int NRG, bool FOLD>
+// U > 0: the radix R0 of u is U (rows unrolled, the per-u partial sums held
+// in registers); U = 0: any R0 <= 4 (partial sums read from shared memory).
+template <typename T, int D, int NRG, bool FOLD, int U = 0>
 __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const unsigned char *stage, unsigned char *pipe,
                                           const int32_t *arows, int lo, int g0, int g1, uint32_t k)
 {
@@ -478,6 +480,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     const uint32_t pipe_s = smem_addr(pipe);
     const uint32_t bus_s = pipe_s + static_cast<uint32_t>(kPipe * NCH * NT * CH);
     const uint32_t arows_s = smem_addr(arows);
+    A bur[U ? U : 1][D];
     if constexpr (FOLD) {
         for (int u = 0; u < R0; ++u) {
             A bu[D];
@@ -490,6 +493,10 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
                 for (int l = 0; l < D; ++l) bu[l] = C::add(bu[l], v[l], k);
             }
             slot_store<D, CH>(bus_s + static_cast<uint32_t>(u * NCH * NT * CH), NT, tid, bu);
+        }
+        if constexpr (U > 0) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) slot_load<D, CH>(bus_s + static_cast<uint32_t>(u * NCH * NT * CH), NT, tid, bur[u]);
         }
     }
     const int gf = nlo;  // the group input
@@ -571,10 +578,15 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
         int32_t o = a[0] + lo;
         if constexpr (FOLD) {
 #pragma unroll
-            for (int u = 0; u < UMAX; ++u)
-                if (u < R0) {
+            for (int u = 0; u < (U ? U : UMAX); ++u)
+                if (U || u < R0) {
                     A bu[D];
-                    slot_load<D, CH>(bus_s + static_cast<uint32_t>(u * NCH * NT * CH), NT, tid, bu);
+                    if constexpr (U > 0) {
+#pragma unroll
+                        for (int l = 0; l < D; ++l) bu[l] = bur[U > 0 ? u : 0][l];
+                    } else {
+                        slot_load<D, CH>(bus_s + static_cast<uint32_t>(u * NCH * NT * CH), NT, tid, bu);
+                    }
                     row(bu, x, ro, o);
                     o += d0;
                 }
@@ -606,7 +618,12 @@ __device__ __forceinline__ void item_fixed(const TaskDev *__restrict__ tkp, cons
         if (tk.pipe) {
             if (tk.R0 <= 4) {
                 switch (tk.F - tk.n_uo) {
-                case 0: item_pipe<T, D, 0, true>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                case 0:  // the radix of u as a template constant: unrolled rows, partial sums in registers
+                    if (tk.R0 == 4) item_pipe<T, D, 0, true, 4>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    else if (tk.R0 == 3) item_pipe<T, D, 0, true, 3>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    else if (tk.R0 == 2) item_pipe<T, D, 0, true, 2>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    else item_pipe<T, D, 0, true>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    break;
                 case 1: item_pipe<T, D, 1, true>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
                 default: item_pipe<T, D, 2, true>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
                 }
