@@ -159,6 +159,12 @@ typedef struct gpube_task_info {
     int64_t rows;           /* separator rows = entries of the output table */
     int32_t *sep;           /* out: separator, descending elimination position */
     int32_t *inputs;        /* out: input ids, in kernel input order */
+    /* out: work decomposition (rows = groups x r0 x lo_extent); inputs
+     * [0, n_lo) depend on the lowest separator digits only, [n_lo, n_group)
+     * are read once per group, [n_group, n_uonly) depend on the fastest hi
+     * digit only, the rest are read per row */
+    int64_t lo_extent, groups;
+    int32_t r0, n_lo, n_group, n_uonly, staged_bytes, pad;
 } gpube_task_info;
 
 typedef struct wcsp wcsp;             /* opaque, library-owned problem         */

@@ -223,7 +223,9 @@ class UtilState:
         ti.inputs = _ptr(ins)
         _check(lib().util_task_info(self.h, int(t), C.byref(ti)))
         return {"var": ti.var, "level": ti.level, "rows": ti.rows, "sep": sep[: ti.n_sep].copy(),
-                "inputs": ins[: ti.n_inputs].copy()}
+                "inputs": ins[: ti.n_inputs].copy(), "lo_extent": ti.lo_extent, "groups": ti.groups,
+                "r0": ti.r0, "n_lo": ti.n_lo, "n_group": ti.n_group, "n_uonly": ti.n_uonly,
+                "staged_bytes": ti.staged_bytes}
 
     def tasks(self):
         return [self.task(t) for t in range(self.info()["n_tasks"])]

@@ -50,7 +50,10 @@ class PlanInfo(C.Structure):
 
 class TaskInfo(C.Structure):
     _fields_ = [("var", C.c_int32), ("level", C.c_int32), ("n_sep", C.c_int32),
-                ("n_inputs", C.c_int32), ("rows", C.c_int64), ("sep", i32p), ("inputs", i32p)]
+                ("n_inputs", C.c_int32), ("rows", C.c_int64), ("sep", i32p), ("inputs", i32p),
+                ("lo_extent", C.c_int64), ("groups", C.c_int64), ("r0", C.c_int32), ("n_lo", C.c_int32),
+                ("n_group", C.c_int32), ("n_uonly", C.c_int32), ("staged_bytes", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 # name -> (restype, argtypes)

@@ -400,6 +400,14 @@ extern "C" int util_task_info(const util_state *s, int32_t t, gpube_task_info *i
     info->rows = T.rows;
     if (info->sep) std::copy(T.sep.begin(), T.sep.end(), info->sep);
     if (info->inputs) std::copy(T.inputs.begin(), T.inputs.end(), info->inputs);
+    info->lo_extent = T.P_lo;
+    info->groups = T.G;
+    info->r0 = T.R0;
+    info->n_lo = T.n_lo;
+    info->n_group = T.n_gi;
+    info->n_uonly = T.n_uo;
+    info->staged_bytes = T.stage_bytes;
+    info->pad = 0;
     return GPUBE_OK;
 }
 
