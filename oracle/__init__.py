@@ -18,6 +18,7 @@ _lib = None
 
 BE, MBE_SEP, MBE_JOINT, MBE_LOG2 = 0, 1, 2, 3
 MODES = {"be": BE, "sep": MBE_SEP, "joint": MBE_JOINT, "log2": MBE_LOG2}
+SEMIRINGS = {"min": 0, "sum": 1}   # min-sum (optimisation) / sum-product (-log Z)
 
 
 class _Problem(C.Structure):
@@ -74,6 +75,10 @@ def _configure(L):
                                       C.POINTER(C.c_ubyte)]
         L.orc_eliminate.argtypes = [P, ip, C.c_int, C.c_int]
         L.orc_eliminate.restype = C.c_void_p
+        L.orc_eliminate_sr.argtypes = [P, ip, C.c_int, C.c_int, C.c_int]
+        L.orc_eliminate_sr.restype = C.c_void_p
+        L.orc_sum_bruteforce.argtypes = [P]
+        L.orc_sum_bruteforce.restype = C.c_double
         L.orc_run_ntasks.argtypes = [C.c_void_p]
         L.orc_run_bound.argtypes = [C.c_void_p]
         L.orc_run_bound.restype = C.c_double
@@ -135,6 +140,25 @@ def bruteforce(inst):
     s = np.zeros(max(inst.n, 1), dtype=np.int32)
     best = lib().orc_bruteforce(p.ref, _iptr(s))
     return best, s[: inst.n]
+
+
+def logz_bruteforce(inst):
+    """-log Z by enumeration, Z = sum over all assignments of exp(-Eq. 1 cost)
+    (real costs; for a WCSP pass counting_instance(inst))."""
+    p = Problem(inst)  # keeps the packed arrays alive during the call
+    return lib().orc_sum_bruteforce(p.ref)
+
+
+def counting_instance(inst):
+    """The weights whose partition function counts a WCSP's consistent
+    solutions (Section 2.1): every entry below the top cost has weight 1
+    (-log weight 0), every entry at or above it weight 0 (+inf).  A real-cost
+    instance is returned unchanged."""
+    if inst.cost_type != "int":
+        return inst
+    from dataclasses import replace
+    tabs = [np.where(np.asarray(t) >= inst.top_k, np.inf, 0.0).astype(np.float64) for t in inst.tables]
+    return replace(inst, tables=tabs, cost_type="real", name=inst.name + "_count")
 
 
 def induced_width(inst, order):
@@ -224,13 +248,18 @@ class Run:
     width: int
 
 
-def eliminate(inst, order, mode="be", z=0, tables=True):
+def eliminate(inst, order, mode="be", z=0, tables=True, semiring="min"):
     """Algorithm 1 (mode "be") or Algorithm 2 (modes "sep", "joint", "log2"
-    with bound z) along ``order``, then the value-assignment phase."""
+    with bound z) along ``order``, then the value-assignment phase.  With
+    semiring "sum" every bucket is eliminated by -log sum exp(-.) instead of
+    min (the bound is then -log Z, or its mini-bucket lower bound, and there
+    is no value phase); a WCSP is first turned into its counting instance."""
+    if semiring == "sum":
+        inst = counting_instance(inst)
     p = Problem(inst)
     o = np.ascontiguousarray(order, dtype=np.int32)
     L = lib()
-    h = L.orc_eliminate(p.ref, _iptr(o), MODES[mode], int(z))
+    h = L.orc_eliminate_sr(p.ref, _iptr(o), MODES[mode], int(z), SEMIRINGS[semiring])
     try:
         nt = L.orc_run_ntasks(h)
         tasks = []
@@ -260,11 +289,13 @@ class Handle:
     """A finished oracle run kept in C memory, read one table at a time
     (for full-size comparisons that do not fit twice in host memory)."""
 
-    def __init__(self, inst, order, mode="be", z=0):
+    def __init__(self, inst, order, mode="be", z=0, semiring="min"):
+        if semiring == "sum":
+            inst = counting_instance(inst)
         self.inst = inst
         self.p = Problem(inst)
         o = np.ascontiguousarray(order, dtype=np.int32)
-        self.h = lib().orc_eliminate(self.p.ref, _iptr(o), MODES[mode], int(z))
+        self.h = lib().orc_eliminate_sr(self.p.ref, _iptr(o), MODES[mode], int(z), SEMIRINGS[semiring])
 
     @property
     def ntasks(self):

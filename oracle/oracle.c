@@ -29,8 +29,20 @@
  *     functions sorted by arity (descending) then creation index;
  *   - MBE value assignment minimises the sum of all functions of the bucket
  *     (all mini-buckets), Section 2.2's example.
+ *   - sum-product (the weighted-counting / partition-function problem the
+ *     conclusions name, and the solution count of Section 2.1): the same
+ *     buckets, with the min over the eliminated variable replaced by
+ *     -log sum_l exp(-s_l), so that the root constants add up to -log Z,
+ *     Z = sum over all assignments of exp(-Eq. 1 cost).  Costs are real
+ *     (-log weights, +inf = weight 0); a WCSP's solutions are counted by
+ *     giving each entry below the top cost weight 1 and the rest weight 0
+ *     (a solution is consistent when no function is at the top cost).  A
+ *     mini-bucket partition eliminates each mini-bucket by its own sum, which
+ *     can only make Z larger (sum_l prod_j g_j <= prod_j sum_l g_j for
+ *     g_j >= 0), so the mini-bucket -log Z is a lower bound, as for min-sum.
+ *     There is no value phase.
  *
- * Parity pins: brute force on tiny instances, the worked examples of
+ * Parity pins: brute force on tiny instances (minimum and -log Z), the worked examples of
  * Sections 2 and 6 (structure and Eq. 3), invariants (BE = optimum, MBE lower
  * bound, cost of the returned assignment), a transfer-matrix DP for grids,
  * component additivity.  The example's optimum value (cost 4, bound 2) is
@@ -146,6 +158,39 @@ double orc_bruteforce(const orc_problem *P, int *sigma_out)
     }
     free(asg);
     return best;
+}
+
+/* -log Z by enumeration (tiny instances only): Z = sum over every complete
+ * assignment of exp(-cost), cost = Eq. 1 (real costs, no saturation).  The
+ * smallest cost c0 is taken out first, -log Z = c0 - log sum exp(c0 - cost),
+ * so that no term underflows as a whole; an instance with no finite-cost
+ * assignment has Z = 0 and -log Z = +inf. */
+double orc_sum_bruteforce(const orc_problem *P)
+{
+    int n = P->n;
+    int *asg = (int *)calloc(n > 0 ? n : 1, sizeof(int));
+    double c0 = INFINITY, z = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        memset(asg, 0, sizeof(int) * (n > 0 ? n : 1));
+        for (;;) {
+            double c = orc_eval(P, asg);
+            if (pass == 0) {
+                if (c < c0) c0 = c;
+            } else {
+                z += exp(c0 - c);
+            }
+            int j = n - 1;
+            while (j >= 0) {
+                if (++asg[j] < P->dom[j]) break;
+                asg[j] = 0;
+                --j;
+            }
+            if (j < 0) break;
+        }
+        if (pass == 0 && !(c0 < INFINITY)) break;
+    }
+    free(asg);
+    return c0 < INFINITY ? c0 - log(z) : INFINITY;
 }
 
 /* ------------------------------------------------------------ primal graph */
@@ -403,6 +448,7 @@ typedef struct {
 } orc_run;
 
 enum { ORC_BE = 0, ORC_MBE_SEP = 1, ORC_MBE_JOINT = 2, ORC_MBE_LOG2 = 3 };
+enum { ORC_MIN_SUM = 0, ORC_SUM_PRODUCT = 1 };
 
 static int fits(const orc_problem *P, int mode, int z, const unsigned char *in_u)
 {
@@ -428,8 +474,10 @@ static int by_arity(const void *a, const void *b)
 }
 
 /* Algorithm 1 (mode ORC_BE) / Algorithm 2 (the other modes) along the given
- * elimination order, followed by the value-assignment phase. */
-orc_run *orc_eliminate(const orc_problem *P, const int *order, int mode, int z)
+ * elimination order.  semiring ORC_MIN_SUM eliminates by min and is followed
+ * by the value-assignment phase; ORC_SUM_PRODUCT eliminates by
+ * -log sum exp(-.) and has no value phase (sigma stays 0, cost is NaN). */
+orc_run *orc_eliminate_sr(const orc_problem *P, const int *order, int mode, int z, int semiring)
 {
     int n = P->n;
     /* A mini-bucket turns one or more live functions into at most one new
@@ -489,7 +537,12 @@ orc_run *orc_eliminate(const orc_problem *P, const int *order, int mode, int z)
         nvb[v] = nb;
         memcpy(vb[v], members, sizeof(int) * nb);
         for (int k = 0; k < nb; ++k) alive[members[k]] = 0;
-        if (nb == 0) continue;
+        if (nb == 0) {
+            /* an empty bucket: min-sum adds nothing; for the sum every value of
+             * v is free, a factor |D_v| of Z */
+            if (semiring == ORC_SUM_PRODUCT) bound += -log((double)P->dom[v]);
+            continue;
+        }
 
         /* partition into mini-buckets: sort by arity desc, creation id asc,
          * then first fit under the bound z */
@@ -553,10 +606,12 @@ orc_run *orc_eliminate(const orc_problem *P, const int *order, int mode, int z)
             T->out = (double *)malloc(sizeof(double) * rows);
             T->arg = (unsigned char *)malloc(rows);
             if (T->nsep > R->width) R->width = T->nsep;
-            /* h(sep) = min over v of the sum of the mini-bucket's functions */
+            /* h(sep) = min over v of the sum of the mini-bucket's functions
+             * (sum-product: -log of the sum over v of exp(-sum)) */
 #pragma omp parallel num_threads(g_threads)
             {
             int *asg = (int *)calloc(n + 1, sizeof(int));
+            double *sv = (double *)malloc(sizeof(double) * P->dom[v]);
 #pragma omp for schedule(static)
             for (long long r = 0; r < rows; ++r) {
                 long long rem = r;
@@ -571,14 +626,22 @@ orc_run *orc_eliminate(const orc_problem *P, const int *order, int mode, int z)
                     double s = 0.0;
                     for (int k = 0; k < nm; ++k) s += func_eval(&fs[mbf[k]], asg);
                     s = clamp_top(P, s);
+                    sv[l] = s;
                     if (l == 0 || s < best) {
                         best = s;
                         bl = l;
                     }
                 }
+                if (semiring == ORC_SUM_PRODUCT && best < INFINITY) {
+                    /* -log sum_l exp(-sv[l]), with the smallest term taken out */
+                    double acc = 0.0;
+                    for (int l = 0; l < P->dom[v]; ++l) acc += exp(best - sv[l]);
+                    best = best - log(acc);
+                }
                 T->out[r] = best;
                 T->arg[r] = (unsigned char)bl;
             }
+            free(sv);
             free(asg);
             }
             free(mbf);
@@ -598,7 +661,7 @@ orc_run *orc_eliminate(const orc_problem *P, const int *order, int mode, int z)
     /* value assignment: reverse elimination order, first argmin of the sum of
      * every function that was in the variable's bucket */
     int *asg = R->sigma;
-    for (int t = n - 1; t >= 0; --t) {
+    for (int t = n - 1; t >= 0 && semiring == ORC_MIN_SUM; --t) {
         int v = order[t];
         double best = 0.0;
         int bl = 0;
@@ -614,7 +677,7 @@ orc_run *orc_eliminate(const orc_problem *P, const int *order, int mode, int z)
         }
         asg[v] = bl;
     }
-    R->cost = orc_eval(P, R->sigma);
+    R->cost = semiring == ORC_MIN_SUM ? orc_eval(P, R->sigma) : NAN;
 
     for (int i = 0; i < nfs; ++i) {
         free(fs[i].vars);
@@ -633,6 +696,11 @@ orc_run *orc_eliminate(const orc_problem *P, const int *order, int mode, int z)
     free(mb_of);
     free(mb_u);
     return R;
+}
+
+orc_run *orc_eliminate(const orc_problem *P, const int *order, int mode, int z)
+{
+    return orc_eliminate_sr(P, order, mode, z, ORC_MIN_SUM);
 }
 
 int orc_run_ntasks(const orc_run *R) { return R->ntasks; }

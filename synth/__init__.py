@@ -17,6 +17,10 @@ from .generators import (  # noqa: F401
     scale_free_wcsp,
     random_network_wcsp,
     disjoint_union,
+    grid_mrf,
+    ising_ring,
+    coloring,
+    with_evidence,
     config_instance,
     TOP_K,
 )

@@ -343,6 +343,64 @@ def disjoint_union(a, b):
                     a.top_k, meta={"parts": [a.n, b.n]})
 
 
+def grid_mrf(rows, cols, d, seed, scale=1.0, unary=True, name=None):
+    """Pairwise Markov random field on a rows x cols grid (variable r*cols+c):
+    real costs (-log potentials) U[0, scale] on every edge (and vertex) table,
+    the workload shape of the grid instances with weights instead of integer
+    costs."""
+    rng = np.random.default_rng(seed)
+    n = rows * cols
+    dom = np.full(n, d, dtype=np.int32)
+    scopes, tables = [], []
+    for r in range(rows):
+        for c in range(cols):
+            v = r * cols + c
+            if unary:
+                scopes.append(np.array([v], dtype=np.int32))
+                tables.append(rng.uniform(0.0, scale, size=d))
+            for u in ((v + 1) if c + 1 < cols else None, (v + cols) if r + 1 < rows else None):
+                if u is not None:
+                    scopes.append(np.array([v, u], dtype=np.int32))
+                    tables.append(rng.uniform(0.0, scale, size=d * d))
+    return Instance(name or f"mrf{rows}x{cols}_d{d}_s{seed}", dom, scopes, tables, "real", TOP_K,
+                    meta={"seed": seed, "rows": rows, "cols": cols})
+
+
+def ising_ring(n, J):
+    """Zero-field Ising ring of n spins s_v = 2 x_v - 1 with coupling J > 0:
+    edge (v, v+1 mod n) has energy J - J s_v s_u >= 0 (0 when aligned, 2J
+    when not), as a real cost table over (x_v, x_u)."""
+    dom = np.full(n, 2, dtype=np.int32)
+    scopes = [np.array(sorted((v, (v + 1) % n)), dtype=np.int32) for v in range(n)]
+    tab = np.array([0.0, 2.0 * J, 2.0 * J, 0.0])
+    return Instance(f"ising_ring{n}_J{J}", dom, scopes, [tab.copy() for _ in range(n)], "real", TOP_K,
+                    meta={"J": J})
+
+
+def coloring(n, edges, q, top_k=1 << 10):
+    """Proper q-colouring as a WCSP: on each edge, equal colours cost the top
+    cost, different colours cost 0."""
+    dom = np.full(n, q, dtype=np.int32)
+    eq = np.where(np.eye(q, dtype=bool).reshape(-1), top_k, 0).astype(np.int64)
+    scopes = [np.array(e, dtype=np.int32) for e in edges]
+    return Instance(f"color{n}_q{q}", dom, scopes, [eq.copy() for _ in edges], "int", top_k)
+
+
+def with_evidence(inst, evidence):
+    """The instance with variables clamped: for each (v, value) a unary table
+    that is 0 at value and infinite (the top cost for a WCSP) elsewhere."""
+    inf = np.inf if inst.cost_type == "real" else inst.top_k
+    scopes = [s.copy() for s in inst.scopes]
+    tables = [t.copy() for t in inst.tables]
+    for v, val in evidence.items():
+        t = np.full(int(inst.dom[v]), inf, dtype=np.float64 if inst.cost_type == "real" else np.int64)
+        t[val] = 0
+        scopes.append(np.array([v], dtype=np.int32))
+        tables.append(t)
+    return Instance(inst.name + "_ev", inst.dom.copy(), scopes, tables, inst.cost_type, inst.top_k,
+                    meta=dict(inst.meta, evidence=dict(evidence)))
+
+
 # --------------------------------------------------------------------------- configurations
 def config_instance(idx, seed=0):
     """The five benchmark workloads by index:

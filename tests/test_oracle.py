@@ -335,3 +335,113 @@ def test_mpe_log_domain_bruteforce(orc):
     assert best == pytest.approx(-np.log(pbest), rel=1e-12)
     run = orc.eliminate(inst, orc.minfill(inst)[0], "be")
     assert run.bound == pytest.approx(best, rel=1e-12)
+
+
+# ------------------------------------ sum-product (-log Z, solution counting)
+def _z_direct(inst):
+    """Z by direct products in probability space over every assignment."""
+    z = 0.0
+    for a in itertools.product(*[range(int(d)) for d in inst.dom]):
+        p = 1.0
+        for s, t in zip(inst.scopes, inst.tables):
+            idx = np.ravel_multi_index([a[v] for v in s], [int(inst.dom[v]) for v in s]) if len(s) else 0
+            p *= np.exp(-float(t[idx]))
+        z += p
+    return z
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_logz_bruteforce_is_the_partition_function(orc, seed):
+    inst = synth.random_small(seed, n=6, dmax=3, n_funcs=8, max_arity=3, cost_type="real", p_top=0.05)
+    z = _z_direct(inst)
+    got = orc.logz_bruteforce(inst)
+    if z == 0.0:
+        assert got == np.inf
+    else:
+        assert got == pytest.approx(-np.log(z), rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_sum_elimination_equals_bruteforce(orc, seed):
+    # exact BE with -log sum exp elimination reaches -log Z on any order;
+    # the instances include variables in no function (a factor |D| each)
+    inst = synth.random_small(seed + 100, n=7, dmax=3, n_funcs=7, max_arity=3, cost_type="real",
+                              p_top=0.05)
+    want = -np.log(_z_direct(inst)) if _z_direct(inst) > 0 else np.inf
+    for order in (orc.minfill(inst)[0], np.arange(inst.n)[::-1]):
+        run = orc.eliminate(inst, order, "be", semiring="sum")
+        assert run.bound == pytest.approx(want, rel=1e-12, abs=1e-12)
+        assert np.isnan(run.cost)
+
+
+def test_bayes_net_partition_function_is_one(orc):
+    # the CPTs of a Bayesian network multiply to a distribution: Z = 1
+    inst = synth.bayes_net_mpe(40, seed=6)
+    run = orc.eliminate(inst, orc.minfill(inst)[0], "be", semiring="sum")
+    assert abs(run.bound) < 1e-9
+
+
+def test_bayes_net_probability_of_evidence(orc):
+    # evidence on x0 (no parents) and x1 (parents within {x0}):
+    # P(x0 = a, x1 = b) = p(a) p(b | a), read off the two CPTs
+    inst = synth.bayes_net_mpe(30, seed=2)
+    assert list(inst.scopes[0]) == [0] and set(inst.scopes[1].tolist()) <= {0, 1}
+    for a in range(int(inst.dom[0])):
+        for b in range(int(inst.dom[1])):
+            ev = synth.with_evidence(inst, {0: a, 1: b})
+            run = orc.eliminate(ev, orc.minfill(ev)[0], "be", semiring="sum")
+            c1 = inst.tables[1][a * int(inst.dom[1]) + b] if len(inst.scopes[1]) == 2 else inst.tables[1][b]
+            assert run.bound == pytest.approx(inst.tables[0][a] + c1, rel=1e-10)
+
+
+def test_ising_ring_closed_form(orc):
+    # zero-field Ising ring: Z = (2 cosh J)^n + (2 sinh J)^n for the energy
+    # -J sum s_v s_u; the tables add J per edge, so -log Z gains n J
+    for n, J in ((8, 0.7), (11, 1.3)):
+        inst = synth.ising_ring(n, J)
+        want = n * J - np.log((2 * np.cosh(J)) ** n + (2 * np.sinh(J)) ** n)
+        assert orc.logz_bruteforce(inst) == pytest.approx(want, rel=1e-12)
+        run = orc.eliminate(inst, orc.minfill(inst)[0], "be", semiring="sum")
+        assert run.bound == pytest.approx(want, rel=1e-12)
+
+
+def test_coloring_counts_closed_forms(orc):
+    # chromatic polynomials: cycle (q-1)^n + (-1)^n (q-1), path q (q-1)^(n-1),
+    # complete graph q! / (q-n)!; an isolated vertex multiplies by q
+    q = 3
+    cyc = synth.coloring(7, [(v, (v + 1) % 7) for v in range(7)], q)
+    path = synth.coloring(6, [(v, v + 1) for v in range(5)], q)
+    k4 = synth.coloring(4, list(itertools.combinations(range(4), 2)), 5)
+    iso = synth.coloring(5, [(0, 1), (1, 2), (2, 3)], q)  # vertex 4 in no constraint
+    cases = [(cyc, (q - 1) ** 7 - (q - 1)), (path, q * (q - 1) ** 5), (k4, 120), (iso, q * q * (q - 1) ** 3)]
+    for inst, count in cases:
+        run = orc.eliminate(inst, orc.minfill(inst)[0], "be", semiring="sum")
+        assert np.exp(-run.bound) == pytest.approx(count, rel=1e-12)
+        assert orc.logz_bruteforce(orc.counting_instance(inst)) == pytest.approx(-np.log(count), rel=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sum_minibuckets_bound_and_exactness(orc, seed):
+    # each mini-bucket summed on its own can only enlarge Z: the mini-bucket
+    # -log Z is a lower bound, exact once the bound admits the whole bucket
+    inst = synth.random_small(seed + 200, n=9, dmax=3, n_funcs=12, max_arity=3, cost_type="real",
+                              p_top=0.0)
+    order, _ = orc.minfill(inst)
+    exact = orc.eliminate(inst, order, "be", semiring="sum")
+    assert exact.bound == pytest.approx(orc.logz_bruteforce(inst), rel=1e-11, abs=1e-11)
+    for z in (1, 2, 3):
+        mb = orc.eliminate(inst, order, "sep", z, semiring="sum")
+        assert mb.bound <= exact.bound + 1e-9
+    full = orc.eliminate(inst, order, "sep", exact.width, semiring="sum")
+    assert full.bound == pytest.approx(exact.bound, rel=1e-12, abs=1e-12)
+
+
+def test_sum_components_multiply(orc):
+    # Z of a disjoint union is the product of the parts' Z
+    a = synth.random_small(41, n=5, dmax=3, n_funcs=6, cost_type="real", p_top=0.0)
+    b = synth.random_small(42, n=4, dmax=3, n_funcs=5, cost_type="real", p_top=0.0)
+    u = synth.disjoint_union(a, b)
+    za = orc.eliminate(a, orc.minfill(a)[0], "be", semiring="sum").bound
+    zb = orc.eliminate(b, orc.minfill(b)[0], "be", semiring="sum").bound
+    zu = orc.eliminate(u, orc.minfill(u)[0], "be", semiring="sum").bound
+    assert zu == pytest.approx(za + zb, rel=1e-12)

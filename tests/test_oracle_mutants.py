@@ -33,6 +33,12 @@ MUTANTS = [
      "if (g_deg[x] != g_deg[y]) return g_deg[x] - g_deg[y];"),
     ("value phase keeps the last variable's value", "        asg[v] = bl;\n    }\n    R->cost",
      "        asg[v] = 0;\n    }\n    R->cost"),
+    ("sum-product eliminates by min", "if (semiring == ORC_SUM_PRODUCT && best < INFINITY) {",
+     "if (0) {"),
+    ("log-sum-exp with the wrong sign", "best = best - log(acc);", "best = best + log(acc);"),
+    ("log-sum-exp without the shift", "acc += exp(best - sv[l]);", "acc += exp(-sv[l]);"),
+    ("free variables not counted", "bound += -log((double)P->dom[v]);", "(void)0;"),
+    ("partition function without the shift", "z += exp(c0 - c);", "z += exp(-c);"),
 ]
 
 
@@ -57,6 +63,15 @@ def _pin_calls():
     for seed in range(2):
         calls.append((f"mbe_bounds_{seed}", lambda o, s=seed: pins.test_mbe_bounds_and_exactness(o, s)))
     calls.append(("dpop_sep", lambda o: pins.test_dpop_separators(o, 0)))
+    calls += [
+        ("logz_direct", lambda o: pins.test_logz_bruteforce_is_the_partition_function(o, 1)),
+        ("sum_bruteforce", lambda o: pins.test_sum_elimination_equals_bruteforce(o, 0)),
+        ("bn_z_one", lambda o: pins.test_bayes_net_partition_function_is_one(o)),
+        ("bn_evidence", lambda o: pins.test_bayes_net_probability_of_evidence(o)),
+        ("ising", lambda o: pins.test_ising_ring_closed_form(o)),
+        ("coloring", lambda o: pins.test_coloring_counts_closed_forms(o)),
+        ("sum_mbe", lambda o: pins.test_sum_minibuckets_bound_and_exactness(o, 0)),
+    ]
     return calls
 
 
