@@ -12,7 +12,8 @@ Also reported on the same line: the HBM roofline of the UTIL kernel, the
 end-to-end solve through the C ABI from host buffers (wcsp_load + be_solve,
 uploads and result copy included), the oracle on the host cores, and the
 secondary workloads (level-batched vs per-bucket MBE on the Erdos-Renyi
-WCSP, MPE in the -log domain, DCOP serving latency).
+WCSP, MPE in the -log domain, sum-product -log Z on the grid shape, DCOP
+serving latency).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU (torchrun): every rank solves its own instance (independent
@@ -179,7 +180,8 @@ def reference_arm(args):
 
 
 def secondary(torch, gb, synth, steps):
-    """Batched vs per-bucket MBE (Erdos-Renyi), MPE entries/s, DCOP serving."""
+    """Batched vs per-bucket MBE (Erdos-Renyi), MPE entries/s, sum-product
+    -log Z on the grid shape, DCOP serving."""
     out = {}
     # level-batched (graph) vs one launch per bucket, MBE log2 <= 16
     inst = synth.config_instance(2, 0)
@@ -219,6 +221,31 @@ def secondary(torch, gb, synth, steps):
                         "util_entries": info["util_entries"], "util_ms": m,
                         "entries_per_s": info["util_entries"] / (m * 1e-3),
                         "gbs": info["alg_bytes"] / (m * 1e-3) / 1e9}
+    # sum-product (-log Z) on the 12x12 grid shape: a pairwise MRF, d = 4
+    inst = synth.grid_mrf(12, 12, 4, seed=0, unary=False)
+    st = gb.UtilState(inst, "sum", order="best", use_graph=True, autotune_cache=TUNE_CACHE)
+    st.bind()
+    thr, rows = st.autotune()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ms = []
+    for k in range(3 + steps):
+        flush.fill_(k & 0xFF)
+        st.run()
+        st.sync()
+        if k >= 3:
+            ms.append(st.times()[0])
+    logz = st.value().bound
+    info = st.info()
+    st.free()
+    del flush
+    m = statistics.median(ms)
+    peak, _ = _peaks()
+    gbs = info["alg_bytes"] / (m * 1e-3) / 1e9
+    out["logz_mrf12x12"] = {"workload": "sum-product -log Z, 12x12 grid MRF, d=4, 264 pairwise tables (fp32)",
+                            "util_entries": info["util_entries"], "util_ms": m,
+                            "entries_per_s": info["util_entries"] / (m * 1e-3), "gbs": gbs,
+                            "hbm_frac": gbs / peak, "block_threads": thr, "rows_per_item": rows,
+                            "neg_log_z": logz}
     out["serving"] = serve_bench(torch, gb, synth, int(os.environ.get("GPUBE_SERVE_REQUESTS", "400")))
     return out
 

@@ -76,7 +76,14 @@ enum gpube_ibound_mode {
     GPUBE_IB_LOG2_ENTRIES = 2 /* product of the mini-bucket's domains <= 2^i_bound        */
 };
 
-enum gpube_kind { GPUBE_KIND_BE = 0, GPUBE_KIND_MBE = 1, GPUBE_KIND_DPOP = 2 };
+enum gpube_kind {
+    GPUBE_KIND_BE = 0,     /* Algorithm 1: min over the eliminated variable        */
+    GPUBE_KIND_MBE = 1,    /* Algorithm 2: mini-buckets under i_bound              */
+    GPUBE_KIND_DPOP = 2,   /* BE along the post-order of a pseudo-tree (Sec. 4.1)  */
+    GPUBE_KIND_SUM = 3,    /* sum-product: BE's buckets, each variable eliminated
+                              by -log sum_l exp(-s_l) (see logz_solve)             */
+    GPUBE_KIND_SUM_MBE = 4 /* sum-product over Algorithm 2's mini-buckets          */
+};
 
 /* ------------------------------------------------------------------ structs */
 
@@ -191,6 +198,24 @@ int be_solve(wcsp *w, const solve_opts *opts, solve_result *res);
  * per variable, the first argmin of the sum of all functions of its bucket. */
 int mbe_solve(wcsp *w, int32_t i_bound, const solve_opts *opts, solve_result *res);
 
+/* Sum-product (the weighted-counting / partition-function / probability-of-
+ * evidence problem that the paper's conclusions name as the extension of
+ * this work; solution counting, Section 2.1).  The buckets are BE's
+ * (i_bound <= 0) or Algorithm 2's mini-buckets (i_bound > 0, read in
+ * opts->ibound_mode); each variable is eliminated by -log sum_l exp(-s_l)
+ * in fp32 instead of min.  res->bound receives -log Z, where
+ *   WCSP_FP32_LOG:  Z = sum over all assignments of exp(-Eq. 1 cost), so for
+ *                   a Bayesian network with evidence clamped by 0 / +inf unary
+ *                   tables, Z is the probability of the evidence;
+ *   WCSP_INT32_SAT: Z = the number of assignments in which no function is at
+ *                   the top cost (each entry < top_k counts as weight 1, the
+ *                   others as weight 0), so exp(-bound) counts solutions.
+ * A variable in no function contributes a factor |D| to Z.  With mini-buckets
+ * the bound is a lower bound on -log Z (each mini-bucket summed on its own
+ * can only enlarge Z).  There is no value phase: res->cost is NaN and
+ * res->assignment is not written.  +inf means Z = 0. */
+int logz_solve(wcsp *w, int32_t i_bound, const solve_opts *opts, solve_result *res);
+
 /* DPOP UTIL phase (Section 4.1) along the pseudo-tree parent[] (host, n
  * entries, -1 = root; NULL = the library's DFS pseudo-tree).  Every
  * constraint must join an ancestor and a descendant of parent[] (EINVAL
@@ -208,7 +233,9 @@ void util_state_free(util_state *s);
 
 /* Host planning only (ordering, buckets, mini-bucket partition, levels,
  * kernel work decomposition); no GPU needed.  kind: enum gpube_kind;
- * i_bound is used by GPUBE_KIND_MBE; parent by GPUBE_KIND_DPOP. */
+ * i_bound is used by GPUBE_KIND_MBE and GPUBE_KIND_SUM_MBE; parent by
+ * GPUBE_KIND_DPOP.  For the sum-product kinds util_value_launch performs the
+ * root reduction only (bound = -log Z, as logz_solve). */
 int util_plan(wcsp *w, int32_t kind, int32_t i_bound, const int32_t *parent,
               const solve_opts *opts, util_state **out);
 int util_plan_info(const util_state *s, gpube_plan_info *info);

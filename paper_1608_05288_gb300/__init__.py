@@ -21,8 +21,8 @@ import numpy as np
 from . import _abi
 from ._abi import (  # noqa: F401
     EAGAIN, ECUDA, EINVAL, ENODEV, ENOMEM, ETIMEDOUT, FP32_LOG, IB_JOINT_VARS, IB_LOG2_ENTRIES,
-    IB_SEP_VARS, INT32_SAT, KIND_BE, KIND_DPOP, KIND_MBE, ORDER_BEST, ORDER_GIVEN, ORDER_MINFILL,
-    ORDER_NATURAL, ORDER_PSEUDOTREE,
+    IB_SEP_VARS, INT32_SAT, KIND_BE, KIND_DPOP, KIND_MBE, KIND_SUM, KIND_SUM_MBE, ORDER_BEST,
+    ORDER_GIVEN, ORDER_MINFILL, ORDER_NATURAL, ORDER_PSEUDOTREE,
 )
 
 ORDERS = {"minfill": ORDER_MINFILL, "best": ORDER_BEST, "given": ORDER_GIVEN,
@@ -185,12 +185,28 @@ def mbe_solve(problem, i_bound, **opts):
     return _result(r, sigma[: w.n])
 
 
+def logz_solve(problem, i_bound=0, **opts):
+    """Sum-product through ``logz_solve``: ``bound`` is -log Z (real costs:
+    Z = sum of exp(-cost) over all assignments; integer WCSP: Z = number of
+    assignments with no function at the top cost), or its mini-bucket lower
+    bound when i_bound > 0.  No assignment; ``cost`` is NaN."""
+    w = _as_wcsp(problem)
+    o = make_opts(**opts)
+    r = _abi.SolveResult()
+    _check(lib().logz_solve(w.h, int(i_bound), C.byref(o), C.byref(r)))
+    return _result(r, None)
+
+
+KINDS = {"be": KIND_BE, "mbe": KIND_MBE, "dpop": KIND_DPOP, "sum": KIND_SUM, "sum_mbe": KIND_SUM_MBE}
+
+
 class UtilState:
     """A planned (and, once bound, device-resident) UTIL phase."""
 
     def __init__(self, problem, kind="be", i_bound=0, parent=None, **opts):
         self.w = _as_wcsp(problem)
-        k = {"be": KIND_BE, "mbe": KIND_MBE, "dpop": KIND_DPOP}[kind] if isinstance(kind, str) else kind
+        k = KINDS[kind] if isinstance(kind, str) else kind
+        self.kind = k
         if k != KIND_DPOP and parent is not None:
             opts.setdefault("parent", parent)  # the pseudo-tree of a GPUBE_ORDER_PSEUDOTREE order
             parent = None
@@ -207,6 +223,7 @@ class UtilState:
     def _wrap(cls, w, h):
         self = cls.__new__(cls)
         self.w, self.h, self.opts, self.arena_tensor, self.bound, self._par = w, h, None, None, True, None
+        self.kind = KIND_DPOP
         return self
 
     def info(self):
@@ -273,7 +290,9 @@ class UtilState:
 
     def fetch(self, t):
         rows = self.task(t)["rows"]
-        cost = np.zeros(max(rows, 1), dtype=np.int32 if self.w.is_int else np.float32)
+        # sum-product tables are fp32 -log weights whatever the problem's cost type
+        fp = not self.w.is_int or self.kind in (KIND_SUM, KIND_SUM_MBE)
+        cost = np.zeros(max(rows, 1), dtype=np.float32 if fp else np.int32)
         arg = np.zeros(max(rows, 1), dtype=np.uint8)
         _check(lib().util_fetch_table(self.h, int(t), cost.ctypes.data_as(C.c_void_p), _ptr(arg, C.c_uint8)))
         return cost[:rows], arg[:rows]
@@ -357,7 +376,7 @@ class Server:
         w = _as_wcsp(problem)
         o = make_opts(**opts)
         par = _i32(parent) if parent is not None else None
-        k = {"be": KIND_BE, "mbe": KIND_MBE, "dpop": KIND_DPOP}[kind]
+        k = KINDS[kind]
         rid = lib().srv_submit(self.h, w.h, k, int(i_bound), _ptr(par), C.byref(o))
         if rid < 0:
             _check(int(rid))

@@ -11,7 +11,7 @@ OK, EINVAL, ENOMEM, ETIMEDOUT, ECUDA, ENODEV, EAGAIN = 0, -22, -12, -110, -1000,
 INT32_SAT, FP32_LOG = 0, 1
 ORDER_MINFILL, ORDER_BEST, ORDER_GIVEN, ORDER_NATURAL, ORDER_PSEUDOTREE = 0, 1, 2, 3, 4
 IB_SEP_VARS, IB_JOINT_VARS, IB_LOG2_ENTRIES = 0, 1, 2
-KIND_BE, KIND_MBE, KIND_DPOP = 0, 1, 2
+KIND_BE, KIND_MBE, KIND_DPOP, KIND_SUM, KIND_SUM_MBE = 0, 1, 2, 3, 4
 
 i32p = C.POINTER(C.c_int32)
 i64p = C.POINTER(C.c_int64)
@@ -64,6 +64,7 @@ SIGNATURES = {
     "solve_opts_init": (None, [C.POINTER(SolveOpts)]),
     "be_solve": (C.c_int, [C.c_void_p, C.POINTER(SolveOpts), C.POINTER(SolveResult)]),
     "mbe_solve": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(SolveOpts), C.POINTER(SolveResult)]),
+    "logz_solve": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(SolveOpts), C.POINTER(SolveResult)]),
     "dpop_util": (C.c_int, [C.c_void_p, i32p, C.POINTER(SolveOpts), C.POINTER(C.c_void_p)]),
     "value_propagate": (C.c_int, [C.c_void_p, i32p, C.POINTER(SolveResult)]),
     "util_state_free": (None, [C.c_void_p]),

@@ -181,6 +181,17 @@ static void build_value_plan(const wcsp &w, Plan &P)
     const int n = w.n;
     ValuePlanH &V = P.value;
     V = ValuePlanH();
+    if (kind_sum(P.kind)) {
+        // sum-product: no assignment and no Eq. 1 evaluation, only the sum
+        // of the root constants (-log Z of each component)
+        V.n_levels = 0;
+        V.lev_off.assign(1, 0);
+        V.vinfo.assign(n, ValueVar{0, 1, 0, 0});
+        for (int v = 0; v < n; ++v) V.vinfo[v].d = w.dom[v];
+        for (const Task &T : P.tasks)
+            if (T.sep.empty()) V.roots.push_back(T.out_off);
+        return;
+    }
     std::vector<std::vector<int32_t>> tasks_of(n);
     for (size_t t = 0; t < P.tasks.size(); ++t) tasks_of[P.tasks[t].var].push_back(static_cast<int32_t>(t));
     std::vector<int32_t> vlev(n, 0);
@@ -209,7 +220,7 @@ static void build_value_plan(const wcsp &w, Plan &P)
         vi.d = w.dom[v];
         if (tasks_of[v].empty()) continue;
         vi.term_off = static_cast<int32_t>(V.terms.size());
-        if (P.kind != GPUBE_KIND_MBE) {
+        if (!kind_mbe(P.kind)) {
             const Task &T = P.tasks[tasks_of[v][0]];
             vi.mode = 1;
             vi.n_terms = 1;
@@ -318,7 +329,7 @@ void gpube_layout(util_state *s)
     for (const Task &T : P.tasks) {
         live += al(T.rows * 4, 128);
         peak = std::max(peak, live);
-        if (P.kind != GPUBE_KIND_MBE)
+        if (!kind_mbe(P.kind))
             for (int fid : T.inputs)
                 if (P.funcs[fid].task >= 0) live -= al(P.funcs[fid].size * 4, 128);
     }
@@ -330,13 +341,34 @@ extern "C" int util_plan(wcsp *w, int32_t kind, int32_t i_bound, const int32_t *
 {
     if (!w || !out) return set_error(GPUBE_EINVAL, "null argument");
     *out = nullptr;
-    if (kind < GPUBE_KIND_BE || kind > GPUBE_KIND_DPOP) return set_error(GPUBE_EINVAL, "unknown kind %d", kind);
+    if (kind < GPUBE_KIND_BE || kind > GPUBE_KIND_SUM_MBE) return set_error(GPUBE_EINVAL, "unknown kind %d", kind);
     solve_opts o;
     if (opts) o = *opts;
     else solve_opts_init(&o);
     const double t0 = now_ms();
     util_state *s = new util_state();
     s->w = w;
+    s->ktype = w->cost_type == WCSP_FP32_LOG ? kKTypeFloat : kKTypeInt;
+    if (kind_sum(kind)) {
+        s->ktype = kKTypeSum;
+        if (w->cost_type == WCSP_INT32_SAT) {
+            // solution counting: weight 1 (-log 0) below the top cost, weight 0
+            // (+inf) at it
+            s->own_w.reset(new wcsp(*w));
+            wcsp &c = *s->own_w;
+            c.cost_type = WCSP_FP32_LOG;
+            c.top_k = 1;
+            c.ftab.resize(c.nf);
+            for (int j = 0; j < c.nf; ++j) {
+                c.ftab[j].resize(c.itab[j].size());
+                for (size_t e = 0; e < c.itab[j].size(); ++e)
+                    c.ftab[j][e] = static_cast<uint32_t>(c.itab[j][e]) >= w->top_k ? INFINITY : 0.0f;
+            }
+            c.itab.clear();
+            c.itab.shrink_to_fit();
+            s->w = &c;
+        }
+    }
     s->opts = o;
     s->batched = o.batched != 0;
     s->use_graph = o.use_graph != 0;
@@ -353,12 +385,12 @@ extern "C" int util_plan(wcsp *w, int32_t kind, int32_t i_bound, const int32_t *
         return set_error(GPUBE_EINVAL, "rows_per_item must be >= 0");
     }
     if (o.rows_per_item) s->cfg.rows_per_item = o.rows_per_item;
-    int rc = build_plan(*w, kind, i_bound, parent, o, s->plan);
+    int rc = build_plan(*s->w, kind, i_bound, parent, o, s->plan);
     if (rc) {
         delete s;
         return rc;
     }
-    shape_tasks(*w, s->plan);
+    shape_tasks(*s->w, s->plan);
     gpube_layout(s);
     if (w->n > 200 * 1024) {
         delete s;
@@ -508,7 +540,7 @@ int gpube_build_descriptors(util_state *s)
     auto blocks_per_sm = [&](int smem) {
         auto it = occ.find(smem);
         if (it != occ.end()) return it->second;
-        int nb = util_max_blocks_per_sm(w.cost_type, NT, smem);
+        int nb = util_max_blocks_per_sm(s->ktype, NT, smem);
         occ[smem] = nb;
         return nb;
     };
@@ -752,7 +784,7 @@ int gpube_enqueue_util(util_state *s, cudaStream_t st)
     const size_t n_counters = std::max<size_t>(s->launches.size(), 1);
     CUDA_TRY(cudaMemsetAsync(s->base + s->counters_off, 0, 4 * n_counters, st));
     for (size_t i = 0; i < s->launches.size(); ++i)
-        CUDA_TRY(launch_util(s->launches[i], s->w->cost_type, s->launch_grid[i], s->cfg.threads, s->launch_smem[i],
+        CUDA_TRY(launch_util(s->launches[i], s->ktype, s->launch_grid[i], s->cfg.threads, s->launch_smem[i],
                              st));
     return GPUBE_OK;
 }
@@ -793,7 +825,7 @@ extern "C" int util_value_launch(util_state *s)
     if (!s || !s->bound) return set_error(GPUBE_EINVAL, "state is not bound");
     if (!s->ran) return set_error(GPUBE_EINVAL, "VALUE phase before the UTIL phase");
     CUDA_TRY(cudaEventRecord(s->ev[2], s->stream));
-    CUDA_TRY(launch_value(s->vdev, s->w->cost_type, s->value_smem, s->stream));
+    CUDA_TRY(launch_value(s->vdev, s->ktype, s->value_smem, s->stream));
     CUDA_TRY(cudaEventRecord(s->ev[3], s->stream));
     s->value_ran = true;
     return GPUBE_OK;
@@ -843,13 +875,14 @@ extern "C" int value_propagate(util_state *s, int32_t *assignment, solve_result 
     int32_t status;
     memcpy(&status, buf.data(), 4);
     if (status == kStatusTimeout) return set_error(GPUBE_ETIMEDOUT, "a bounded device-side wait gave up");
-    if (assignment) memcpy(assignment, buf.data() + 24, 4 * static_cast<size_t>(n));
+    const bool sum = kind_sum(s->plan.kind);  // no assignment, no Eq. 1 cost
+    if (assignment && !sum) memcpy(assignment, buf.data() + 24, 4 * static_cast<size_t>(n));
     if (res) {
         double r[2];
         memcpy(r, buf.data() + 8, 16);
         res->bound = r[0];
-        res->cost = r[1];
-        if (res->assignment && res->assignment != assignment)
+        res->cost = sum ? NAN : r[1];
+        if (!sum && res->assignment && res->assignment != assignment)
             memcpy(res->assignment, buf.data() + 24, 4 * static_cast<size_t>(n));
         fill_stats(s, res);
         float a = 0.f, b = 0.f;
@@ -890,7 +923,7 @@ static std::string tune_key(const util_state *s)
     const Plan &P = s->plan;
     std::ostringstream k;
     k << "k" << P.kind << "_t" << P.tasks.size() << "_l" << P.n_levels << "_e" << P.util_entries << "_c"
-      << s->w->cost_type << "_b" << (s->batched ? 1 : 0);
+      << s->ktype << "_b" << (s->batched ? 1 : 0);
     return k.str();
 }
 
@@ -980,6 +1013,11 @@ extern "C" int mbe_solve(wcsp *w, int32_t i_bound, const solve_opts *opts, solve
     return solve_common(w, GPUBE_KIND_MBE, i_bound, nullptr, opts, res);
 }
 
+extern "C" int logz_solve(wcsp *w, int32_t i_bound, const solve_opts *opts, solve_result *res)
+{
+    return solve_common(w, i_bound > 0 ? GPUBE_KIND_SUM_MBE : GPUBE_KIND_SUM, i_bound, nullptr, opts, res);
+}
+
 extern "C" int dpop_util(wcsp *w, const int32_t *parent, const solve_opts *opts, util_state **out)
 {
     if (!w || !out) return set_error(GPUBE_EINVAL, "null argument");
@@ -1033,6 +1071,7 @@ extern "C" int util_bucket(int32_t cost_type, int32_t top_k, int32_t m, const in
     w.dom[m] = d;
     util_state s;
     s.w = &w;
+    s.ktype = cost_type == WCSP_FP32_LOG ? kKTypeFloat : kKTypeInt;
     Plan &P = s.plan;
     P.kind = GPUBE_KIND_BE;
     P.order.resize(m + 1);

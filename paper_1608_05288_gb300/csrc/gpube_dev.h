@@ -16,6 +16,12 @@ constexpr unsigned long long kWaitNs = 1000000000ull;  // time limit of every de
 constexpr int kStatusOk = 0;
 constexpr int kStatusTimeout = 1;
 
+// UTIL kernel instantiations: int32 min-sum (WCSP_INT32_SAT), fp32 min-sum
+// (WCSP_FP32_LOG), fp32 sum-product
+constexpr int kKTypeInt = 0;
+constexpr int kKTypeFloat = 1;
+constexpr int kKTypeSum = 2;
+
 // Kernel variants: the eliminated domain class times the input-count class.
 // D class 0 = any domain size (runtime loop, one thread per row); 1..7 =
 // domain 2..8; 8 = wide domains (>= 32 values: a warp per row, lanes over the

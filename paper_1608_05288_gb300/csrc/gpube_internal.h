@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -76,6 +77,10 @@ struct Task {
     int32_t stage_bytes = 0;
 };
 
+// Mini-bucket partition (Algorithm 2) / sum-product elimination, by kind.
+inline bool kind_mbe(int kind) { return kind == GPUBE_KIND_MBE || kind == GPUBE_KIND_SUM_MBE; }
+inline bool kind_sum(int kind) { return kind == GPUBE_KIND_SUM || kind == GPUBE_KIND_SUM_MBE; }
+
 struct Plan {
     int32_t kind = GPUBE_KIND_BE;
     int32_t i_bound = 0, ibound_mode = GPUBE_IB_SEP_VARS;
@@ -112,11 +117,12 @@ void task_strides(const wcsp &w, const Plan &P, const Task &T, std::vector<int32
 void shape_tasks(const wcsp &w, Plan &P);
 
 // kernels (util_kernel.cu)
-cudaError_t launch_util(const LaunchDev &L, int cost_type, int grid, int threads, int smem, cudaStream_t s);
-int util_max_blocks_per_sm(int cost_type, int threads, int smem);
+// ktype: kKTypeInt / kKTypeFloat / kKTypeSum (gpube_dev.h)
+cudaError_t launch_util(const LaunchDev &L, int ktype, int grid, int threads, int smem, cudaStream_t s);
+int util_max_blocks_per_sm(int ktype, int threads, int smem);
 cudaError_t launch_expand(const ExpandDev *tasks, const int64_t *prefix, int n_tasks, int64_t total,
                           const int32_t *pool, int num_sms, cudaStream_t s);
-cudaError_t launch_value(const ValueDev &V, int cost_type, int smem, cudaStream_t s);
+cudaError_t launch_value(const ValueDev &V, int ktype, int smem, cudaStream_t s);
 cudaError_t kernels_init_device();
 cudaError_t launch_selftest_wait(int32_t *status, unsigned long long limit_ns, cudaStream_t s);
 
@@ -137,6 +143,8 @@ struct DescLayout {
 
 struct util_state {
     const wcsp *w = nullptr;
+    std::unique_ptr<wcsp> own_w;  // the counting weights of a WCSP (sum-product kinds), when w points here
+    int ktype = 0;                // UTIL kernel instantiation (kKType*)
     gpube::Plan plan;
     gpube::LaunchCfg cfg;
     solve_opts opts{};

@@ -76,6 +76,7 @@ extern "C" int util_bucket_noalloc(int32_t cost_type, int32_t top_k, int32_t m, 
     w.dom[m] = d;
     util_state s;
     s.w = &w;
+    s.ktype = cost_type == WCSP_FP32_LOG ? kKTypeFloat : kKTypeInt;
     Plan &P = s.plan;
     P.kind = GPUBE_KIND_BE;
     P.order.resize(m + 1);

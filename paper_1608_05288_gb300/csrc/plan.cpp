@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <numeric>
 
@@ -282,7 +283,7 @@ int build_plan(const wcsp &w, int kind, int i_bound, const int32_t *parent, cons
     P.kind = kind;
     P.i_bound = i_bound;
     P.ibound_mode = o.ibound_mode;
-    if (kind == GPUBE_KIND_MBE && (o.ibound_mode < 0 || o.ibound_mode > 2))
+    if (kind_mbe(kind) && (o.ibound_mode < 0 || o.ibound_mode > 2))
         return set_error(GPUBE_EINVAL, "unknown ibound_mode %d", o.ibound_mode);
     if (o.lo_target > 0) P.lo_target = o.lo_target;
     if (o.stage_max_entries > 0) P.stage_max_entries = o.stage_max_entries;
@@ -352,11 +353,16 @@ int build_plan(const wcsp &w, int kind, int i_bound, const int32_t *parent, cons
     }
 
     // 3. Algorithm 1 / 2: buckets, partitions, bucket functions
-    const bool mbe = (kind == GPUBE_KIND_MBE);
+    const bool mbe = kind_mbe(kind);
     for (int t = 0; t < n; ++t) {
         const int v = P.order[t];
         std::vector<int32_t> B = bucket[v];
-        if (B.empty()) continue;
+        if (B.empty()) {
+            // a variable in no function: nothing to minimise; in the sum each
+            // of its values counts, a factor |D_v| of Z
+            if (kind_sum(kind)) P.const_sum += -std::log(static_cast<double>(w.dom[v]));
+            continue;
+        }
         std::stable_sort(B.begin(), B.end(), [&](int a, int b) {
             if (P.funcs[a].scope.size() != P.funcs[b].scope.size())
                 return P.funcs[a].scope.size() > P.funcs[b].scope.size();

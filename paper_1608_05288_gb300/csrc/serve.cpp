@@ -13,6 +13,7 @@
 // work of requests of different sizes overlaps on the device.  A request
 // whose last level has run gets its VALUE kernel and an asynchronous copy of
 // its result; it is retired (memory returned) once that copy has landed.
+#include <math.h>
 #include <string.h>
 
 #include <algorithm>
@@ -116,6 +117,7 @@ struct gpube_server {
     cudaEvent_t dev_ev[2] = {nullptr, nullptr};
     bool dev_used[2] = {false, false};
     int flip = 0;
+    int64_t key_turn = 0;  // which group of compatible requests launches next
     int32_t *work = nullptr;  // [0..1] counters, [2] status
     int num_sms = 0, threads = 256;
     int64_t launches = 0, max_inflight = 0;
@@ -244,9 +246,12 @@ static int retire(gpube_server *s)
             double rr[2];
             memcpy(rr, pb + 8, 16);
             const int n = r->st->w->n;
-            r->sigma.assign(reinterpret_cast<const int32_t *>(pb + 24), reinterpret_cast<const int32_t *>(pb + 24) + n);
+            const bool sum = kind_sum(r->st->plan.kind);  // no assignment, no Eq. 1 cost
+            if (!sum)
+                r->sigma.assign(reinterpret_cast<const int32_t *>(pb + 24),
+                                reinterpret_cast<const int32_t *>(pb + 24) + n);
             r->res.bound = rr[0];
-            r->res.cost = rr[1];
+            r->res.cost = sum ? NAN : rr[1];
             const Plan &P = r->st->plan;
             r->res.induced_width = P.width;
             r->res.n_tasks = static_cast<int32_t>(P.tasks.size());
@@ -279,7 +284,19 @@ extern "C" int srv_step(gpube_server *s)
     int rc = retire(s);
     if (!rc) rc = admit(s);
     if (rc) return rc;
-    // merge the next level of every running request into one launch
+    // merge the next level of every running request into one launch.  One
+    // launch runs one kernel instantiation with one top cost, so only the
+    // requests that share them are merged; when the running requests differ
+    // (integer / fp32 costs, sum-product, another top cost) the groups take
+    // turns, one per step.
+    std::vector<std::pair<int, uint32_t>> keys;
+    for (Request *r : s->active)
+        if (r->state == kActive && r->next_level < r->st->plan.n_levels) {
+            const std::pair<int, uint32_t> k(r->st->ktype, r->st->w->top_k);
+            if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
+        }
+    std::pair<int, uint32_t> key(kKTypeInt, 0u);
+    if (!keys.empty()) key = keys[static_cast<size_t>(s->key_turn++) % keys.size()];
     std::vector<TaskDev> tds;
     std::vector<Request *> finishing;
     int smem = 0, pipe_d = 0;
@@ -290,7 +307,7 @@ extern "C" int srv_step(gpube_server *s)
             r->up_waited = true;
         }
         const Plan &P = r->st->plan;
-        if (r->next_level < P.n_levels) {
+        if (r->next_level < P.n_levels && r->st->ktype == key.first && r->st->w->top_k == key.second) {
             const TaskDev *td = reinterpret_cast<const TaskDev *>(
                 r->st->host_blob.data() + (r->st->dl.taskdev - r->st->desc_off));
             for (int i = P.level_off[r->next_level]; i < P.level_off[r->next_level + 1]; ++i) {
@@ -333,15 +350,14 @@ extern "C" int srv_step(gpube_server *s)
         L.total_items = static_cast<int32_t>(tot);
         L.counter = s->work + b;
         L.status = s->work + 2;
-        L.top_k = s->active.front()->st->w->top_k;
+        L.top_k = key.second;
         L.arows_off = static_cast<int32_t>(al(smem, 16));
         L.pipe_off = L.arows_off + (pipe_d ? kMaxPipeRows * 16 : 0);
         if (pipe_d) smem = L.pipe_off + kPipe * s->threads * pipe_d * 4 + 4 * s->threads * pipe_d * 4;
         SRV_TRY(cudaMemsetAsync(L.counter, 0, 4, s->stream));
-        const int cost_type = s->active.front()->st->w->cost_type;
-        const int64_t cap = static_cast<int64_t>(util_max_blocks_per_sm(cost_type, s->threads, smem)) * s->num_sms;
+        const int64_t cap = static_cast<int64_t>(util_max_blocks_per_sm(key.first, s->threads, smem)) * s->num_sms;
         const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(tot, cap)));
-        SRV_TRY(launch_util(L, cost_type, grid, s->threads, smem, s->stream));
+        SRV_TRY(launch_util(L, key.first, grid, s->threads, smem, s->stream));
         SRV_TRY(cudaEventRecord(s->dev_ev[b], s->stream));
         s->dev_used[b] = true;
         s->launches++;
@@ -349,7 +365,7 @@ extern "C" int srv_step(gpube_server *s)
     for (Request *r : finishing) {
         util_state *st = r->st;
         st->ran = true;
-        SRV_TRY(launch_value(st->vdev, st->w->cost_type, st->value_smem, s->stream));
+        SRV_TRY(launch_value(st->vdev, st->ktype, st->value_smem, s->stream));
         const size_t need = 24 + 4 * static_cast<size_t>(std::max(st->w->n, 1));
         SRV_TRY(cudaMemcpyAsync(s->pinned[r->slot], st->base + st->status_off, need, cudaMemcpyDeviceToHost,
                                 s->stream));

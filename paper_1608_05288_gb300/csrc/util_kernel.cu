@@ -8,15 +8,18 @@
 
 namespace gpube {
 
-// defined in util_kernel_i32.cu / util_kernel_f32.cu
+// defined in util_kernel_i32.cu / util_kernel_f32.cu / util_kernel_sum.cu
 cudaError_t launch_util_i32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s);
 cudaError_t launch_util_f32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s);
+cudaError_t launch_util_sum(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s);
 int util_max_blocks_i32(int threads, int smem);
 int util_max_blocks_f32(int threads, int smem);
+int util_max_blocks_sum(int threads, int smem);
 cudaError_t launch_value_i32(const ValueDev &V, int smem, cudaStream_t s);
 cudaError_t launch_value_f32(const ValueDev &V, int smem, cudaStream_t s);
 cudaError_t kernel_attrs_i32(int max_smem);
 cudaError_t kernel_attrs_f32(int max_smem);
+cudaError_t kernel_attrs_sum(int max_smem);
 
 // ------------------------------------------------------ plan expansion
 // Fills every task's A and B offset tables from its compact plan: the row h
@@ -119,15 +122,24 @@ cudaError_t launch_selftest_wait(int32_t *status, unsigned long long limit_ns, c
 }
 
 // -------------------------------------------------------- host launchers
-cudaError_t launch_util(const LaunchDev &L, int cost_type, int grid, int threads, int smem, cudaStream_t s)
+// ktype: kKTypeInt (int32 min-sum), kKTypeFloat (fp32 min-sum), kKTypeSum
+// (fp32 sum-product)
+cudaError_t launch_util(const LaunchDev &L, int ktype, int grid, int threads, int smem, cudaStream_t s)
 {
-    return cost_type == 1 ? launch_util_f32(L, grid, threads, smem, s)
-                          : launch_util_i32(L, grid, threads, smem, s);
+    switch (ktype) {
+    case kKTypeFloat: return launch_util_f32(L, grid, threads, smem, s);
+    case kKTypeSum: return launch_util_sum(L, grid, threads, smem, s);
+    default: return launch_util_i32(L, grid, threads, smem, s);
+    }
 }
 
-int util_max_blocks_per_sm(int cost_type, int threads, int smem)
+int util_max_blocks_per_sm(int ktype, int threads, int smem)
 {
-    return cost_type == 1 ? util_max_blocks_f32(threads, smem) : util_max_blocks_i32(threads, smem);
+    switch (ktype) {
+    case kKTypeFloat: return util_max_blocks_f32(threads, smem);
+    case kKTypeSum: return util_max_blocks_sum(threads, smem);
+    default: return util_max_blocks_i32(threads, smem);
+    }
 }
 
 cudaError_t launch_expand(const ExpandDev *tasks, const int64_t *prefix, int n_tasks, int64_t total,
@@ -140,9 +152,9 @@ cudaError_t launch_expand(const ExpandDev *tasks, const int64_t *prefix, int n_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_value(const ValueDev &V, int cost_type, int smem, cudaStream_t s)
+cudaError_t launch_value(const ValueDev &V, int ktype, int smem, cudaStream_t s)
 {
-    return cost_type == 1 ? launch_value_f32(V, smem, s) : launch_value_i32(V, smem, s);
+    return ktype == kKTypeInt ? launch_value_i32(V, smem, s) : launch_value_f32(V, smem, s);
 }
 
 // Once per device (current device): allow every kernel the device's largest
@@ -162,6 +174,7 @@ cudaError_t kernels_init_device()
     e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess) e = kernel_attrs_i32(max_smem - 1024);
     if (e == cudaSuccess) e = kernel_attrs_f32(max_smem - 1024);
+    if (e == cudaSuccess) e = kernel_attrs_sum(max_smem - 1024);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }

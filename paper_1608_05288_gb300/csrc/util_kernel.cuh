@@ -1,5 +1,6 @@
-// UTIL and VALUE kernel templates for sm_103a; instantiated per cost type in
-// util_kernel_i32.cu and util_kernel_f32.cu.
+// UTIL and VALUE kernel templates for sm_103a; instantiated per cost type and
+// elimination operator in util_kernel_i32.cu, util_kernel_f32.cu and
+// util_kernel_sum.cu.
 #pragma once
 // UTIL-table kernels for sm_103a.
 //
@@ -7,7 +8,8 @@
 // UTIL messages): for each separator row r and each value l of the
 // eliminated variable x_i it gathers one entry of every input table, sums
 // them (saturating at the top cost for integer WCSPs, Section 2; fp32 for
-// -log p costs, Section 3), and keeps the minimum and first argmin over l.
+// -log p costs, Section 3), and keeps the minimum and first argmin over l
+// (or, for the sum-product problem, -log of the sum over l of exp(-sum)).
 // This fuses the paper's Gpu::Aggregate (Eq. 3 gather, Section 6.3) and
 // Gpu::Eliminate (Section 6.4): no joint table is materialised, every input
 // entry is read where it is needed, the output is written once.
@@ -128,7 +130,9 @@ template <typename T> struct Cost;
 // Integer WCSP costs in [0, k]: sums saturate at k (k means "not allowed").
 // Both operands are <= k < 2^31, so their uint32 sum cannot wrap.
 template <> struct Cost<int32_t> {
+    using val = int32_t;
     using acc = uint32_t;
+    static constexpr bool kSum = false;
     static __device__ __forceinline__ acc from(int32_t v) { return static_cast<uint32_t>(v); }
     static __device__ __forceinline__ acc add(acc a, int32_t v, uint32_t k)
     {
@@ -140,13 +144,57 @@ template <> struct Cost<int32_t> {
 
 // -log p costs in fp32; +inf (p = 0) propagates through the sum.
 template <> struct Cost<float> {
+    using val = float;
     using acc = float;
+    static constexpr bool kSum = false;
     static __device__ __forceinline__ acc from(float v) { return v; }
     static __device__ __forceinline__ acc add(acc a, float v, uint32_t) { return a + v; }
     static __device__ __forceinline__ float store(acc a) { return a; }
 };
 
-template <typename T> using A_t = typename Cost<T>::acc;
+// Sum-product in the -log domain (weighted counting, partition function):
+// the terms add as fp32 -log weights, and x_i is eliminated by
+// -log sum_l exp(-s_l) instead of min_l s_l.  The argmin is still recorded.
+struct SumProduct : Cost<float> {
+    static constexpr bool kSum = true;
+};
+
+constexpr float kInfF = __builtin_huge_valf();
+
+// Elimination of one row's D sums: the first minimum and its index; for the
+// sum-product, -log sum exp(-acc[l]) taken relative to that minimum (every
+// exponent <= 0, one term is 1), +inf when every term is +inf.
+template <typename C, int D>
+__device__ __forceinline__ typename C::acc reduce_run(const typename C::acc (&acc)[D], int &bi)
+{
+    using A = typename C::acc;
+    A best = acc[0];
+    bi = 0;
+#pragma unroll
+    for (int l = 1; l < D; ++l)
+        if (acc[l] < best) {
+            best = acc[l];
+            bi = l;
+        }
+    if constexpr (C::kSum) {
+        if (best < kInfF) {
+            float t = 0.f;
+#pragma unroll
+            for (int l = 0; l < D; ++l) t += __expf(best - acc[l]);
+            best -= __logf(t);
+        }
+    }
+    return best;
+}
+
+// The same elimination for values that arrive one at a time (runtime domain
+// size) keeps a running minimum best and, for the sum-product, the running
+// sum t of exp(best - s_l), rescaled whenever the minimum drops; lse_value
+// turns the pair into -log sum exp(-s_l).
+__device__ __forceinline__ float lse_value(float best, float t)
+{
+    return best < kInfF ? best - __logf(t) : best;
+}
 
 // The d entries of one x_i-run, loaded with the widest aligned vector:
 // offsets are multiples of d, so d % 4 == 0 runs are 16-byte aligned.
@@ -281,12 +329,12 @@ __device__ __forceinline__ void load_ints(const int32_t *p, int32_t (&a)[N])
 }
 
 // Fixed domain D, any number of inputs (offsets reread per input).
-template <typename T, int D>
+template <typename C, int D>
 __device__ __noinline__ void item_fixed_anyF(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo,
                                                 int g0, int g1, uint32_t k)
 {
     const TaskDev tk = *tkp;
-    using C = Cost<T>;
+    using T = typename C::val;
     using A = typename C::acc;
     const int F = tk.F;
     const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * tk.sb;
@@ -304,14 +352,8 @@ __device__ __noinline__ void item_fixed_anyF(const TaskDev *__restrict__ tkp, co
 #pragma unroll
                 for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
             }
-            A best = acc[0];
-            int bi = 0;
-#pragma unroll
-            for (int l = 1; l < D; ++l)
-                if (acc[l] < best) {
-                    best = acc[l];
-                    bi = l;
-                }
+            int bi;
+            const A best = reduce_run<C, D>(acc, bi);
             const int o = Ar[0] + u * du[0] + lo;
             out[o] = C::store(best);
             tk.arg[o] = static_cast<uint8_t>(bi);
@@ -327,12 +369,12 @@ __device__ __noinline__ void item_fixed_anyF(const TaskDev *__restrict__ tkp, co
 // row adds its NR runs, takes the min and first argmin over x_i and writes
 // both.  Row offsets advance by the stride of u: a row costs NR vector
 // loads, the adds, the argmin and two stores.
-template <typename T, int D, int FC, int NR>
+template <typename C, int D, int FC, int NR>
 __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo, int g0,
                                               int g1, uint32_t k)
 {
     const TaskDev tk = *tkp;
-    using C = Cost<T>;
+    using T = typename C::val;
     using A = typename C::acc;
     constexpr int SA = FC + 1;
     constexpr int SB = (FC + 3) / 4 * 4;
@@ -417,14 +459,8 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
 #pragma unroll
                         for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
                     }
-                    A best = acc[0];
-                    int bi = 0;
-#pragma unroll
-                    for (int l = 1; l < D; ++l)
-                        if (acc[l] < best) {
-                            best = acc[l];
-                            bi = l;
-                        }
+                    int bi;
+                    const A best = reduce_run<C, D>(acc, bi);
                     out[oo[j]] = C::store(best);
                     arg[oo[j]] = static_cast<uint8_t>(bi);
                     oo[j] += d0;
@@ -448,12 +484,12 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
 // clamped entry equals k and the first argmin is 0.
 // U > 0: the radix R0 of u is U (rows unrolled, the per-u partial sums held
 // in registers); U = 0: any R0 <= 4 (partial sums read from shared memory).
-template <typename T, int D, int NRG, bool FOLD, int U = 0>
+template <typename C, int D, int NRG, bool FOLD, int U = 0>
 __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const unsigned char *stage, unsigned char *pipe,
                                           const int32_t *arows, int lo, int g0, int g1, uint32_t k)
 {
     const TaskDev tk = *tkp;
-    using C = Cost<T>;
+    using T = typename C::val;
     using A = typename C::acc;
     constexpr bool kInt = std::is_same<T, int32_t>::value;
     constexpr int FC = 3, SA = 4, SB = 4, UMAX = 4;
@@ -549,6 +585,14 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
                 best = acc[l];
                 bi = l;
             }
+        if constexpr (C::kSum) {
+            if (best < kInfF) {
+                float t = 0.f;
+#pragma unroll
+                for (int l = 0; l < D; ++l) t += __expf(best - acc[l]);
+                best -= __logf(t);
+            }
+        }
         if constexpr (NRG == 0 && kInt) {
             if (best >= k) {
                 best = k;
@@ -609,7 +653,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     cp_async_wait<0>();
 }
 
-template <typename T, int D, int FC>
+template <typename C, int D, int FC>
 __device__ __forceinline__ void item_fixed(const TaskDev *__restrict__ tkp, const TaskDev &tk,
                                            const unsigned char *stage, unsigned char *pipe, const int32_t *arows,
                                            int lo, int g0, int g1, uint32_t k)
@@ -619,42 +663,42 @@ __device__ __forceinline__ void item_fixed(const TaskDev *__restrict__ tkp, cons
             if (tk.R0 <= 4) {
                 switch (tk.F - tk.n_uo) {
                 case 0:  // the radix of u as a template constant: unrolled rows, partial sums in registers
-                    if (tk.R0 == 4) item_pipe<T, D, 0, true, 4>(tkp, stage, pipe, arows, lo, g0, g1, k);
-                    else if (tk.R0 == 3) item_pipe<T, D, 0, true, 3>(tkp, stage, pipe, arows, lo, g0, g1, k);
-                    else if (tk.R0 == 2) item_pipe<T, D, 0, true, 2>(tkp, stage, pipe, arows, lo, g0, g1, k);
-                    else item_pipe<T, D, 0, true>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    if (tk.R0 == 4) item_pipe<C, D, 0, true, 4>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    else if (tk.R0 == 3) item_pipe<C, D, 0, true, 3>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    else if (tk.R0 == 2) item_pipe<C, D, 0, true, 2>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    else item_pipe<C, D, 0, true>(tkp, stage, pipe, arows, lo, g0, g1, k);
                     break;
-                case 1: item_pipe<T, D, 1, true>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
-                default: item_pipe<T, D, 2, true>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                case 1: item_pipe<C, D, 1, true>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                default: item_pipe<C, D, 2, true>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
                 }
             } else {
                 switch (tk.F - tk.n_gi) {
-                case 0: item_pipe<T, D, 0, false>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
-                case 1: item_pipe<T, D, 1, false>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
-                default: item_pipe<T, D, 2, false>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                case 0: item_pipe<C, D, 0, false>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                case 1: item_pipe<C, D, 1, false>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                default: item_pipe<C, D, 2, false>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
                 }
             }
             return;
         }
     }
     switch (tk.F - tk.n_gi) {
-    case 0: item_fixed_nr<T, D, FC, 0>(tkp, stage, lo, g0, g1, k); break;
-    case 1: item_fixed_nr<T, D, FC, 1>(tkp, stage, lo, g0, g1, k); break;
-    case 2: item_fixed_nr<T, D, FC, 2>(tkp, stage, lo, g0, g1, k); break;
+    case 0: item_fixed_nr<C, D, FC, 0>(tkp, stage, lo, g0, g1, k); break;
+    case 1: item_fixed_nr<C, D, FC, 1>(tkp, stage, lo, g0, g1, k); break;
+    case 2: item_fixed_nr<C, D, FC, 2>(tkp, stage, lo, g0, g1, k); break;
     default:
-        if constexpr (FC <= 3) item_fixed_nr<T, D, FC, 3>(tkp, stage, lo, g0, g1, k);
-        else item_fixed_anyF<T, D>(tkp, stage, lo, g0, g1, k);
+        if constexpr (FC <= 3) item_fixed_nr<C, D, FC, 3>(tkp, stage, lo, g0, g1, k);
+        else item_fixed_anyF<C, D>(tkp, stage, lo, g0, g1, k);
         break;
     }
 }
 
 // Any domain size (runtime loop over x_i's values), at most FC inputs.
-template <typename T, int FC>
+template <typename C, int FC>
 __device__ __noinline__ void item_anyD(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo, int g0,
                                           int g1, uint32_t k)
 {
     const TaskDev tk = *tkp;
-    using C = Cost<T>;
+    using T = typename C::val;
     using A = typename C::acc;
     constexpr int SA = FC + 1;
     constexpr int SB = (FC + 3) / 4 * 4;
@@ -676,16 +720,21 @@ __device__ __noinline__ void item_anyD(const TaskDev *__restrict__ tkp, const un
             for (int f = 0; f < FC; ++f) q[f] = (f < F) ? p[f] + (a[1 + f] + u * du[1 + f]) : nullptr;
             A best = A(0);
             int bi = 0;
+            float t = 1.f;  // sum-product only
             for (int l = 0; l < d; ++l) {
                 A s = C::from(q[0][l]);
 #pragma unroll
                 for (int f = 1; f < FC; ++f)
                     if (f < F) s = C::add(s, q[f][l], k);
                 if (l == 0 || s < best) {
+                    if constexpr (C::kSum) t = l == 0 ? 1.f : t * __expf(s - best) + 1.f;
                     best = s;
                     bi = l;
+                } else if constexpr (C::kSum) {
+                    if (s < kInfF) t += __expf(best - s);
                 }
             }
+            if constexpr (C::kSum) best = lse_value(best, t);
             const int o = a[0] + u * du[0] + lo;
             out[o] = C::store(best);
             tk.arg[o] = static_cast<uint8_t>(bi);
@@ -694,12 +743,12 @@ __device__ __noinline__ void item_anyD(const TaskDev *__restrict__ tkp, const un
 }
 
 // Any domain size, any number of inputs.
-template <typename T>
+template <typename C>
 __device__ __noinline__ void item_anyD_anyF(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo,
                                                int g0, int g1, uint32_t k)
 {
     const TaskDev tk = *tkp;
-    using C = Cost<T>;
+    using T = typename C::val;
     using A = typename C::acc;
     const int F = tk.F, d = tk.d;
     const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * tk.sb;
@@ -710,15 +759,20 @@ __device__ __noinline__ void item_anyD_anyF(const TaskDev *__restrict__ tkp, con
         for (int u = 0; u < tk.R0; ++u) {
             A best = A(0);
             int bi = 0;
+            float t = 1.f;  // sum-product only
             for (int l = 0; l < d; ++l) {
                 A s = A(0);
                 for (int f = 0; f < F; ++f)
                     s = C::add(s, input_base<T>(tk.in[f], stage)[Ar[1 + f] + u * du[1 + f] + Brow[f] + l], k);
                 if (l == 0 || s < best) {
+                    if constexpr (C::kSum) t = l == 0 ? 1.f : t * __expf(s - best) + 1.f;
                     best = s;
                     bi = l;
+                } else if constexpr (C::kSum) {
+                    if (s < kInfF) t += __expf(best - s);
                 }
             }
+            if constexpr (C::kSum) best = lse_value(best, t);
             const int o = Ar[0] + u * du[0] + lo;
             out[o] = C::store(best);
             tk.arg[o] = static_cast<uint8_t>(bi);
@@ -731,12 +785,12 @@ __device__ __noinline__ void item_anyD_anyF(const TaskDev *__restrict__ tkp, con
 // coalesced warp access per 32 values, each lane keeps its first minimum and
 // the warp combines (value, index) pairs by shuffles, ties to the lower index.
 // The warp covers the 32 rows lo0 .. lo0 + 31 of its lanes in turn.
-template <typename T, int FC>
+template <typename C, int FC>
 __device__ __noinline__ void item_wide(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo,
                                        int g0, int g1, uint32_t k)
 {
     const TaskDev tk = *tkp;
-    using C = Cost<T>;
+    using T = typename C::val;
     using A = typename C::acc;
     constexpr int kRuns = 8;  // 8 x 32 lanes >= 255 values
     const int lane = threadIdx.x & 31;
@@ -784,6 +838,19 @@ __device__ __noinline__ void item_wide(const TaskDev *__restrict__ tkp, const un
                         bi = oi;
                     }
                 }
+                if constexpr (C::kSum) {
+                    // every lane now holds the row minimum: sum exp(min - s_l)
+                    // over the lane's values, then over the warp
+                    if (best < kInfF) {
+                        float t = 0.f;
+#pragma unroll
+                        for (int j = 0; j < kRuns; ++j)
+                            if (lane + 32 * j < d) t += __expf(best - acc[j]);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                        best -= __logf(t);
+                    }
+                }
                 if (lane == 0) {
                     const int o = Ar[0] + u * du[0] + rlo;
                     out[o] = C::store(best);
@@ -794,51 +861,51 @@ __device__ __noinline__ void item_wide(const TaskDev *__restrict__ tkp, const un
     }
 }
 
-template <typename T, int D>
+template <typename C, int D>
 __device__ __forceinline__ void dispatch_f(const TaskDev *__restrict__ tkp, const TaskDev &tk, int fc,
                                            const unsigned char *stage, unsigned char *pipe, const int32_t *arows,
                                            int lo, int h0, int h1, uint32_t k)
 {
     if constexpr (D == 0) {
         switch (fc) {
-        case 0: item_anyD<T, 3>(tkp, stage, lo, h0, h1, k); break;
-        case 1: item_anyD<T, 7>(tkp, stage, lo, h0, h1, k); break;
-        default: item_anyD_anyF<T>(tkp, stage, lo, h0, h1, k); break;
+        case 0: item_anyD<C, 3>(tkp, stage, lo, h0, h1, k); break;
+        case 1: item_anyD<C, 7>(tkp, stage, lo, h0, h1, k); break;
+        default: item_anyD_anyF<C>(tkp, stage, lo, h0, h1, k); break;
         }
     } else {
         switch (fc) {
-        case 0: item_fixed<T, D, 3>(tkp, tk, stage, pipe, arows, lo, h0, h1, k); break;
-        case 1: item_fixed<T, D, 7>(tkp, tk, stage, pipe, arows, lo, h0, h1, k); break;
-        default: item_fixed_anyF<T, D>(tkp, stage, lo, h0, h1, k); break;
+        case 0: item_fixed<C, D, 3>(tkp, tk, stage, pipe, arows, lo, h0, h1, k); break;
+        case 1: item_fixed<C, D, 7>(tkp, tk, stage, pipe, arows, lo, h0, h1, k); break;
+        default: item_fixed_anyF<C, D>(tkp, stage, lo, h0, h1, k); break;
         }
     }
 }
 
-template <typename T>
+template <typename C>
 __device__ __forceinline__ void dispatch(const TaskDev *__restrict__ tkp, const TaskDev &tk,
                                          const unsigned char *stage, unsigned char *pipe, const int32_t *arows,
                                          int lo, int h0, int h1, uint32_t k)
 {
     const int dc = tk.variant / kNumFClass, fc = tk.variant % kNumFClass;
     switch (dc) {
-    case 1: dispatch_f<T, 2>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
-    case 2: dispatch_f<T, 3>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
-    case 3: dispatch_f<T, 4>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
-    case 4: dispatch_f<T, 5>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
-    case 5: dispatch_f<T, 6>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
-    case 6: dispatch_f<T, 7>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
-    case 7: dispatch_f<T, 8>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 1: dispatch_f<C, 2>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 2: dispatch_f<C, 3>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 3: dispatch_f<C, 4>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 4: dispatch_f<C, 5>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 5: dispatch_f<C, 6>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 6: dispatch_f<C, 7>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 7: dispatch_f<C, 8>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     case kDClassWide:
-        if (fc == 0) item_wide<T, 3>(tkp, stage, lo, h0, h1, k);
-        else if (fc == 1) item_wide<T, 7>(tkp, stage, lo, h0, h1, k);
-        else item_wide<T, 0>(tkp, stage, lo, h0, h1, k);
+        if (fc == 0) item_wide<C, 3>(tkp, stage, lo, h0, h1, k);
+        else if (fc == 1) item_wide<C, 7>(tkp, stage, lo, h0, h1, k);
+        else item_wide<C, 0>(tkp, stage, lo, h0, h1, k);
         break;
-    default: dispatch_f<T, 0>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    default: dispatch_f<C, 0>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     }
 }
 
 // ------------------------------------------------------------- kernel
-template <typename T>
+template <typename C>
 __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
 {
     extern __shared__ __align__(128) unsigned char stage[];
@@ -909,7 +976,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
         // one thread per row, except the wide variant: whole warps, one row at a time
         const bool wide = tk.variant / kNumFClass == kDClassWide;
         if (wide ? (lo & ~31) < tk.P_lo : lo < tk.P_lo)
-            dispatch<T>(L.tasks + a, tk, stage, stage + L.pipe_off, reinterpret_cast<const int32_t *>(stage + L.arows_off),
+            dispatch<C>(L.tasks + a, tk, stage, stage + L.pipe_off, reinterpret_cast<const int32_t *>(stage + L.arows_off),
                         lo, h0, h1, L.top_k);
 
         __syncthreads();

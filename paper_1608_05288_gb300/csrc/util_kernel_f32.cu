@@ -5,14 +5,14 @@ namespace gpube {
 
 cudaError_t launch_util_f32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s)
 {
-    util_kernel<float><<<grid, threads, smem, s>>>(L);
+    util_kernel<Cost<float>><<<grid, threads, smem, s>>>(L);
     return cudaGetLastError();
 }
 
 int util_max_blocks_f32(int threads, int smem)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, util_kernel<float>, threads, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, util_kernel<Cost<float>>, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -29,7 +29,7 @@ cudaError_t launch_value_f32(const ValueDev &V, int smem, cudaStream_t s)
 // device maximum, once per device, outside any stream capture.
 cudaError_t kernel_attrs_f32(int max_smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(util_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    cudaError_t e = cudaFuncSetAttribute(util_kernel<Cost<float>>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(value_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     return e;

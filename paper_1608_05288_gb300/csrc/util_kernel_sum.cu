@@ -1,0 +1,30 @@
+// Instantiation of the UTIL kernel for the sum-product problem: fp32 -log
+// weights, each variable eliminated by -log sum exp(-.) (the weighted counting
+// / partition function extension of the conclusions; solution counting,
+// Section 2.1).  Its root reduction runs on the fp32 VALUE kernel.
+#include "util_kernel.cuh"
+
+namespace gpube {
+
+cudaError_t launch_util_sum(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s)
+{
+    util_kernel<SumProduct><<<grid, threads, smem, s>>>(L);
+    return cudaGetLastError();
+}
+
+int util_max_blocks_sum(int threads, int smem)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, util_kernel<SumProduct>, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t kernel_attrs_sum(int max_smem)
+{
+    return cudaFuncSetAttribute(util_kernel<SumProduct>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+}
+
+}  // namespace gpube

@@ -169,3 +169,25 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_abi, "LIB_PATH", str(tmp_path / "libgpube.so"))
     with pytest.raises(RuntimeError):
         gb.WCSP(synth.paper_example())
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_sum_plans_match_oracle(orc, seed):
+    # the sum-product kinds plan BE's buckets / Algorithm 2's mini-buckets
+    inst = synth.random_small(seed + 70, n=10, dmax=4, n_funcs=14, max_arity=3, cost_type="real")
+    o, _ = orc.minfill(inst)
+    st = gb.UtilState(inst, "sum", order="given", order_array=o)
+    assert _lib_structure(st) == _orc_structure(orc.eliminate(inst, o, "be", tables=False, semiring="sum"))
+    for z in (1, 2, 4):
+        st = gb.UtilState(inst, "sum_mbe", z, order="given", order_array=o, ibound_mode="joint")
+        want = orc.eliminate(inst, o, "joint", z, tables=False, semiring="sum")
+        assert _lib_structure(st) == _orc_structure(want)
+
+
+def test_sum_counting_plan_of_integer_wcsp(orc):
+    # counting an integer WCSP plans the same buckets and stores fp32 tables
+    inst = synth.random_small(5, n=10, dmax=4, n_funcs=14, max_arity=3, p_top=0.3)
+    be = gb.UtilState(inst, "be")
+    sm = gb.UtilState(inst, "sum")
+    assert _lib_structure(be) == _lib_structure(sm)
+    assert sm.info()["alg_bytes"] == be.info()["alg_bytes"]
