@@ -125,6 +125,9 @@ typedef struct solve_opts {
     void *stream;              /* cudaStream_t, NULL = legacy default stream            */
     const char *autotune_cache;/* file for tuned launch parameters, or NULL             */
     int32_t device;            /* CUDA device ordinal                                    */
+    const int32_t *evidence_vars; /* [n_evidence_vars] host: variables that util_condition
+                                  may clamp on this plan (distinct), or NULL             */
+    int32_t n_evidence_vars;
 } solve_opts;
 
 /* Result of a solve.  assignment, when non-NULL, is caller-owned host memory
@@ -268,6 +271,20 @@ int util_fetch_table(util_state *s, int32_t t, void *cost_host, uint8_t *arg_hos
  * opts.autotune_cache when given.  Writes the chosen values to *threads and
  * *rows_per_item (either may be NULL). */
 int util_autotune(util_state *s, int32_t *threads, int32_t *rows_per_item);
+
+/* Conditioning: clamp variables to values for the following runs of the same
+ * plan, without planning or binding again (evidence in a Bayesian network,
+ * Section 3; the repeated mini-bucket bounds of a search that conditions on
+ * partial assignments, Section 9).  Each variable must be one of the
+ * evidence_vars the plan was made with: the plan holds, per such variable, a
+ * unary function in that variable's bucket, all zero while the variable is
+ * free; clamping x_v to a sets it to 0 at a and to the top cost (fp32:
+ * +inf) elsewhere.  vals[i] = -1 frees vars[i]; variables not listed keep
+ * their state.  On a bound state the new tables are copied on the bound
+ * stream (ordered after the work already queued there), so the next
+ * util_run uses them, graph replays included.  EINVAL for an undeclared
+ * variable or a value outside its domain (nothing is changed then). */
+int util_condition(util_state *s, int32_t n, const int32_t *vars, const int32_t *vals);
 
 /* Device time in ms of the last util_run / VALUE phase (after util_sync). */
 int util_last_times(util_state *s, double *util_ms, double *value_ms);

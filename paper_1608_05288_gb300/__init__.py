@@ -95,7 +95,7 @@ class WCSP:
 def make_opts(order="minfill", order_array=None, parent=None, ibound_mode="sep", batched=True,
               use_graph=False, block_threads=0, rows_per_item=0, lo_target=0,
               stage_max_entries=0, arena=None, arena_bytes=0, stream=None,
-              autotune_cache=None, device=0):
+              autotune_cache=None, device=0, evidence_vars=None):
     o = _abi.SolveOpts()
     lib().solve_opts_init(C.byref(o))
     o.order_kind = ORDERS[order] if isinstance(order, str) else int(order)
@@ -125,6 +125,11 @@ def make_opts(order="minfill", order_array=None, parent=None, ibound_mode="sep",
         keep.append(b)
         o.autotune_cache = b
     o.device = int(device)
+    if evidence_vars is not None and len(evidence_vars):
+        ev = _i32(evidence_vars)
+        keep.append(ev)
+        o.evidence_vars = _ptr(ev)
+        o.n_evidence_vars = len(ev)
     o._keep = keep
     return o
 
@@ -296,6 +301,13 @@ class UtilState:
         arg = np.zeros(max(rows, 1), dtype=np.uint8)
         _check(lib().util_fetch_table(self.h, int(t), cost.ctypes.data_as(C.c_void_p), _ptr(arg, C.c_uint8)))
         return cost[:rows], arg[:rows]
+
+    def condition(self, evidence):
+        """Clamp evidence variables for the next runs: {var: value}, value
+        -1 (or None) frees the variable (``util_condition``)."""
+        vs = _i32(list(evidence.keys()))
+        xs = _i32([-1 if x is None else int(x) for x in evidence.values()])
+        _check(lib().util_condition(self.h, len(vs), _ptr(vs), _ptr(xs)))
 
     def autotune(self):
         a, b = C.c_int32(), C.c_int32()

@@ -30,7 +30,8 @@ class SolveOpts(C.Structure):
                 ("block_threads", C.c_int32), ("rows_per_item", C.c_int32),
                 ("lo_target", C.c_int32), ("stage_max_entries", C.c_int32),
                 ("arena", C.c_void_p), ("arena_bytes", C.c_size_t), ("stream", C.c_void_p),
-                ("autotune_cache", C.c_char_p), ("device", C.c_int32)]
+                ("autotune_cache", C.c_char_p), ("device", C.c_int32),
+                ("evidence_vars", i32p), ("n_evidence_vars", C.c_int32)]
 
 
 class SolveResult(C.Structure):
@@ -65,6 +66,7 @@ SIGNATURES = {
     "be_solve": (C.c_int, [C.c_void_p, C.POINTER(SolveOpts), C.POINTER(SolveResult)]),
     "mbe_solve": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(SolveOpts), C.POINTER(SolveResult)]),
     "logz_solve": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(SolveOpts), C.POINTER(SolveResult)]),
+    "util_condition": (C.c_int, [C.c_void_p, C.c_int32, i32p, i32p]),
     "dpop_util": (C.c_int, [C.c_void_p, i32p, C.POINTER(SolveOpts), C.POINTER(C.c_void_p)]),
     "value_propagate": (C.c_int, [C.c_void_p, i32p, C.POINTER(SolveResult)]),
     "util_state_free": (None, [C.c_void_p]),

@@ -346,6 +346,16 @@ extern "C" int util_plan(wcsp *w, int32_t kind, int32_t i_bound, const int32_t *
     if (opts) o = *opts;
     else solve_opts_init(&o);
     const double t0 = now_ms();
+    if (o.n_evidence_vars < 0 || (o.n_evidence_vars > 0 && !o.evidence_vars))
+        return set_error(GPUBE_EINVAL, "bad evidence_vars");
+    {
+        std::vector<char> seen(w->n, 0);
+        for (int i = 0; i < o.n_evidence_vars; ++i) {
+            const int v = o.evidence_vars[i];
+            if (v < 0 || v >= w->n || seen[v]) return set_error(GPUBE_EINVAL, "evidence variable %d", v);
+            seen[v] = 1;
+        }
+    }
     util_state *s = new util_state();
     s->w = w;
     s->ktype = w->cost_type == WCSP_FP32_LOG ? kKTypeFloat : kKTypeInt;
@@ -369,7 +379,25 @@ extern "C" int util_plan(wcsp *w, int32_t kind, int32_t i_bound, const int32_t *
             s->w = &c;
         }
     }
+    if (o.n_evidence_vars > 0) {
+        // one unary function per evidence variable, appended after the
+        // problem's functions, all zero (free) until util_condition
+        if (!s->own_w) s->own_w.reset(new wcsp(*w));
+        wcsp &c = *s->own_w;
+        s->ev_fid0 = c.nf;
+        for (int i = 0; i < o.n_evidence_vars; ++i) {
+            const int v = o.evidence_vars[i];
+            c.scope.push_back({v});
+            if (c.cost_type == WCSP_FP32_LOG) c.ftab.emplace_back(c.dom[v], 0.0f);
+            else c.itab.emplace_back(c.dom[v], 0);
+            s->ev_vars.push_back(v);
+            s->ev_val.push_back(-1);
+        }
+        c.nf += o.n_evidence_vars;
+        s->w = &c;
+    }
     s->opts = o;
+    s->opts.evidence_vars = nullptr;  // not kept: the caller owns the array
     s->batched = o.batched != 0;
     s->use_graph = o.use_graph != 0;
     s->device = o.device;
@@ -838,6 +866,50 @@ extern "C" int util_sync(util_state *s)
     int32_t status = 0;
     CUDA_TRY(cudaMemcpy(&status, s->base + s->status_off, 4, cudaMemcpyDeviceToHost));
     if (status == kStatusTimeout) return set_error(GPUBE_ETIMEDOUT, "a bounded device-side wait gave up");
+    return GPUBE_OK;
+}
+
+extern "C" int util_condition(util_state *s, int32_t n, const int32_t *vars, const int32_t *vals)
+{
+    if (!s || n < 0 || (n > 0 && (!vars || !vals))) return set_error(GPUBE_EINVAL, "bad argument");
+    if (s->ev_vars.empty()) {
+        if (n == 0) return GPUBE_OK;
+        return set_error(GPUBE_EINVAL, "the plan has no evidence variables");
+    }
+    wcsp &c = *s->own_w;  // present whenever ev_vars is non-empty
+    std::vector<int> slot(n);
+    for (int i = 0; i < n; ++i) {
+        auto it = std::find(s->ev_vars.begin(), s->ev_vars.end(), vars[i]);
+        if (it == s->ev_vars.end()) return set_error(GPUBE_EINVAL, "variable %d is not an evidence variable", vars[i]);
+        slot[i] = static_cast<int>(it - s->ev_vars.begin());
+        if (vals[i] < -1 || vals[i] >= c.dom[vars[i]])
+            return set_error(GPUBE_EINVAL, "value %d outside the domain of variable %d", vals[i], vars[i]);
+    }
+    for (int i = 0; i < n; ++i) {
+        const int e = slot[i], j = s->ev_fid0 + e, a = vals[i];
+        s->ev_val[e] = a;
+        if (c.cost_type == WCSP_FP32_LOG)
+            for (int l = 0; l < c.dom[vars[i]]; ++l) c.ftab[j][l] = (a < 0 || l == a) ? 0.0f : INFINITY;
+        else
+            for (int l = 0; l < c.dom[vars[i]]; ++l)
+                c.itab[j][l] = (a < 0 || l == a) ? 0 : static_cast<int32_t>(c.top_k);
+    }
+    if (!s->bound) return GPUBE_OK;  // util_bind uploads the current tables
+    // the evidence tables are the last originals of the arena: one copy of
+    // their span (the host buffer is staged before cudaMemcpyAsync returns)
+    const Plan &P = s->plan;
+    const int j0 = s->ev_fid0, j1 = c.nf - 1;
+    const size_t a0 = P.funcs[j0].off, a1 = P.funcs[j1].off + static_cast<size_t>(P.funcs[j1].size) * 4;
+    std::vector<unsigned char> buf(a1 - a0, 0);
+    for (int j = j0; j <= j1; ++j) {
+        const size_t d = static_cast<size_t>(P.funcs[j].size) * 4;
+        memcpy(buf.data() + (P.funcs[j].off - a0),
+               c.cost_type == WCSP_FP32_LOG ? static_cast<const void *>(c.ftab[j].data())
+                                            : static_cast<const void *>(c.itab[j].data()),
+               d);
+    }
+    CUDA_TRY(cudaSetDevice(s->device));
+    CUDA_TRY(cudaMemcpyAsync(s->base + a0, buf.data(), buf.size(), cudaMemcpyHostToDevice, s->stream));
     return GPUBE_OK;
 }
 

@@ -143,8 +143,13 @@ struct DescLayout {
 
 struct util_state {
     const wcsp *w = nullptr;
-    std::unique_ptr<wcsp> own_w;  // the counting weights of a WCSP (sum-product kinds), when w points here
+    std::unique_ptr<wcsp> own_w;  // the problem as planned, when it differs from the caller's: the
+                                  // counting weights of a WCSP (sum-product kinds) and/or the
+                                  // evidence functions appended (w points here then)
     int ktype = 0;                // UTIL kernel instantiation (kKType*)
+    std::vector<int32_t> ev_vars; // variables util_condition may clamp
+    std::vector<int32_t> ev_val;  // their current value, -1 = free
+    int32_t ev_fid0 = 0;          // function id of ev_vars[0]'s unary (the others follow)
     gpube::Plan plan;
     gpube::LaunchCfg cfg;
     solve_opts opts{};

@@ -386,15 +386,23 @@ def coloring(n, edges, q, top_k=1 << 10):
     return Instance(f"color{n}_q{q}", dom, scopes, [eq.copy() for _ in edges], "int", top_k)
 
 
-def with_evidence(inst, evidence):
+def with_evidence(inst, evidence, declared=None):
     """The instance with variables clamped: for each (v, value) a unary table
-    that is 0 at value and infinite (the top cost for a WCSP) elsewhere."""
+    that is 0 at value and infinite (the top cost for a WCSP) elsewhere.
+    With ``declared`` (a list of variables), one unary table is appended per
+    declared variable in that order instead: the clamp when the variable is
+    in ``evidence`` (and its value is not -1 / None), all zero otherwise."""
     inf = np.inf if inst.cost_type == "real" else inst.top_k
+    dt = np.float64 if inst.cost_type == "real" else np.int64
     scopes = [s.copy() for s in inst.scopes]
     tables = [t.copy() for t in inst.tables]
-    for v, val in evidence.items():
-        t = np.full(int(inst.dom[v]), inf, dtype=np.float64 if inst.cost_type == "real" else np.int64)
-        t[val] = 0
+    for v in (declared if declared is not None else list(evidence.keys())):
+        val = evidence.get(v)
+        if val is None or val < 0:
+            t = np.zeros(int(inst.dom[v]), dtype=dt)
+        else:
+            t = np.full(int(inst.dom[v]), inf, dtype=dt)
+            t[val] = 0
         scopes.append(np.array([v], dtype=np.int32))
         tables.append(t)
     return Instance(inst.name + "_ev", inst.dom.copy(), scopes, tables, inst.cost_type, inst.top_k,

@@ -191,3 +191,29 @@ def test_sum_counting_plan_of_integer_wcsp(orc):
     sm = gb.UtilState(inst, "sum")
     assert _lib_structure(be) == _lib_structure(sm)
     assert sm.info()["alg_bytes"] == be.info()["alg_bytes"]
+
+
+def test_evidence_plan_matches_oracle(orc):
+    # evidence variables add one unary function each, after the problem's own
+    inst = synth.random_small(11, n=10, dmax=4, n_funcs=14, max_arity=3)
+    ev_vars = [7, 2, 9]
+    o, _ = orc.minfill(inst)
+    aug = synth.with_evidence(inst, {}, declared=ev_vars)
+    for kind, mode, z in (("be", "be", 0), ("mbe", "sep", 2)):
+        st = gb.UtilState(inst, kind, z, order="given", order_array=o, ibound_mode="sep", evidence_vars=ev_vars)
+        assert _lib_structure(st) == _orc_structure(orc.eliminate(aug, o, mode, z, tables=False))
+
+
+def test_condition_validates():
+    inst = synth.random_small(12, n=6, dmax=3, n_funcs=8)
+    st = gb.UtilState(inst, "be", evidence_vars=[1, 3])
+    st.condition({1: 0, 3: None})            # before binding: kept for the upload
+    with pytest.raises(gb.GpubeError):
+        st.condition({2: 0})                 # not declared
+    with pytest.raises(gb.GpubeError):
+        st.condition({1: int(inst.dom[1])})  # outside the domain
+    with pytest.raises(gb.GpubeError):
+        gb.UtilState(inst, "be", evidence_vars=[1, 1])
+    plain = gb.UtilState(inst, "be")
+    with pytest.raises(gb.GpubeError):
+        plain.condition({1: 0})
