@@ -811,9 +811,11 @@ int gpube_enqueue_util(util_state *s, cudaStream_t st)
 {
     const size_t n_counters = std::max<size_t>(s->launches.size(), 1);
     CUDA_TRY(cudaMemsetAsync(s->base + s->counters_off, 0, 4 * n_counters, st));
+    // consecutive levels: each launch may be scheduled while the previous one
+    // drains (it waits for it before reading any table)
     for (size_t i = 0; i < s->launches.size(); ++i)
         CUDA_TRY(launch_util(s->launches[i], s->ktype, s->launch_grid[i], s->cfg.threads, s->launch_smem[i],
-                             st));
+                             st, i > 0));
     return GPUBE_OK;
 }
 

@@ -117,8 +117,10 @@ void task_strides(const wcsp &w, const Plan &P, const Task &T, std::vector<int32
 void shape_tasks(const wcsp &w, Plan &P);
 
 // kernels (util_kernel.cu)
-// ktype: kKTypeInt / kKTypeFloat / kKTypeSum (gpube_dev.h)
-cudaError_t launch_util(const LaunchDev &L, int ktype, int grid, int threads, int smem, cudaStream_t s);
+// ktype: kKTypeInt / kKTypeFloat / kKTypeSum (gpube_dev.h); pdl: programmatic
+// dependent launch after the previous UTIL launch on the stream
+cudaError_t launch_util(const LaunchDev &L, int ktype, int grid, int threads, int smem, cudaStream_t s,
+                        bool pdl = false);
 int util_max_blocks_per_sm(int ktype, int threads, int smem);
 cudaError_t launch_expand(const ExpandDev *tasks, const int64_t *prefix, int n_tasks, int64_t total,
                           const int32_t *pool, int num_sms, cudaStream_t s);

@@ -9,9 +9,9 @@
 namespace gpube {
 
 // defined in util_kernel_i32.cu / util_kernel_f32.cu / util_kernel_sum.cu
-cudaError_t launch_util_i32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s);
-cudaError_t launch_util_f32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s);
-cudaError_t launch_util_sum(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s);
+cudaError_t launch_util_i32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl);
+cudaError_t launch_util_f32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl);
+cudaError_t launch_util_sum(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl);
 int util_max_blocks_i32(int threads, int smem);
 int util_max_blocks_f32(int threads, int smem);
 int util_max_blocks_sum(int threads, int smem);
@@ -124,12 +124,12 @@ cudaError_t launch_selftest_wait(int32_t *status, unsigned long long limit_ns, c
 // -------------------------------------------------------- host launchers
 // ktype: kKTypeInt (int32 min-sum), kKTypeFloat (fp32 min-sum), kKTypeSum
 // (fp32 sum-product)
-cudaError_t launch_util(const LaunchDev &L, int ktype, int grid, int threads, int smem, cudaStream_t s)
+cudaError_t launch_util(const LaunchDev &L, int ktype, int grid, int threads, int smem, cudaStream_t s, bool pdl)
 {
     switch (ktype) {
-    case kKTypeFloat: return launch_util_f32(L, grid, threads, smem, s);
-    case kKTypeSum: return launch_util_sum(L, grid, threads, smem, s);
-    default: return launch_util_i32(L, grid, threads, smem, s);
+    case kKTypeFloat: return launch_util_f32(L, grid, threads, smem, s, pdl);
+    case kKTypeSum: return launch_util_sum(L, grid, threads, smem, s, pdl);
+    default: return launch_util_i32(L, grid, threads, smem, s, pdl);
     }
 }
 

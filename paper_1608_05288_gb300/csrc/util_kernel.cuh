@@ -904,6 +904,17 @@ __device__ __forceinline__ void dispatch(const TaskDev *__restrict__ tkp, const 
     }
 }
 
+// Programmatic dependent launch (consecutive levels of one run): a launch may
+// start while the previous one drains; griddep_wait blocks until the previous
+// launch has completed and its writes are visible, griddep_launch_dependents
+// lets the next launch be scheduled (its CTAs still wait before reading).
+// Both are no-ops for a launch without a programmatic predecessor / successor.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------- kernel
 template <typename C>
 __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
@@ -917,10 +928,15 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
     if (tid == 0) {
         mbar_init(&bar, 1);
         s_staged = -1;
-        s_item[0] = atomicAdd(L.counter, 1);
+        s_item[0] = atomicAdd(L.counter, 1);  // this launch's own counter, cleared before the run
         fence_mbar_init();
     }
     __syncthreads();
+    // the next level may be scheduled now: its CTAs become resident only as
+    // this launch's CTAs exit (every CTA of this launch is resident already)
+    griddep_launch_dependents();
+    // tables written by the previous level are read only after this point
+    griddep_wait();
     uint32_t phase = 0;
     int it = 0;
     int item = s_item[0];
@@ -983,6 +999,26 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
         item = s_item[nb];
         ++it;
     }
+}
+
+// Host: launch one UTIL kernel instantiation; with pdl the launch carries the
+// programmatic stream serialization attribute (it may be scheduled while its
+// predecessor on the stream drains, see griddep_wait).
+template <typename K>
+inline cudaError_t launch_util_kernel(K kernel, const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s,
+                                      bool pdl)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(static_cast<unsigned>(threads));
+    cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, L);
 }
 
 // ------------------------------------------------------------- VALUE

@@ -3,10 +3,9 @@
 
 namespace gpube {
 
-cudaError_t launch_util_f32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s)
+cudaError_t launch_util_f32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl)
 {
-    util_kernel<Cost<float>><<<grid, threads, smem, s>>>(L);
-    return cudaGetLastError();
+    return launch_util_kernel(util_kernel<Cost<float>>, L, grid, threads, smem, s, pdl);
 }
 
 int util_max_blocks_f32(int threads, int smem)

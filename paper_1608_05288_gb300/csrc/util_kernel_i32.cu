@@ -3,10 +3,9 @@
 
 namespace gpube {
 
-cudaError_t launch_util_i32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s)
+cudaError_t launch_util_i32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl)
 {
-    util_kernel<Cost<int32_t>><<<grid, threads, smem, s>>>(L);
-    return cudaGetLastError();
+    return launch_util_kernel(util_kernel<Cost<int32_t>>, L, grid, threads, smem, s, pdl);
 }
 
 int util_max_blocks_i32(int threads, int smem)

@@ -6,10 +6,9 @@
 
 namespace gpube {
 
-cudaError_t launch_util_sum(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s)
+cudaError_t launch_util_sum(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl)
 {
-    util_kernel<SumProduct><<<grid, threads, smem, s>>>(L);
-    return cudaGetLastError();
+    return launch_util_kernel(util_kernel<SumProduct>, L, grid, threads, smem, s, pdl);
 }
 
 int util_max_blocks_sum(int threads, int smem)
