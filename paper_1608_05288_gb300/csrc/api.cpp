@@ -493,12 +493,40 @@ static const void *func_ptr(const util_state *s, int fid)
 // Rebuild the launch-configuration-dependent descriptors (TaskDev, InDev,
 // work-item prefixes) and the static ones (expansion plan, value plan) into
 // the host blob that mirrors [desc_off, value_off + value_bytes).
+// Upper bounds of every function's entries (integer costs): an original's
+// largest entry, a bucket function's min(k, sum of its inputs' bounds) (its
+// entries are minima of such sums).  Tables the library cannot read (caller
+// device tables) and the evidence tables (rewritten after binding) are
+// bounded by k.
+static std::vector<uint64_t> upper_bounds(const util_state *s)
+{
+    const wcsp &w = *s->w;
+    const Plan &P = s->plan;
+    const uint64_t k = w.top_k;
+    std::vector<uint64_t> ub(P.funcs.size(), k);
+    if (w.cost_type != WCSP_INT32_SAT) return ub;
+    const int ev0 = s->ev_vars.empty() ? w.nf : s->ev_fid0;
+    for (int j = 0; j < w.nf && j < ev0; ++j) {
+        if (P.funcs[j].ext || static_cast<size_t>(j) >= w.itab.size() || w.itab[j].empty()) continue;
+        uint64_t m = 0;
+        for (int32_t v : w.itab[j]) m = std::max<uint64_t>(m, static_cast<uint32_t>(v));
+        ub[j] = std::min(m, k);
+    }
+    for (size_t t = 0; t < P.tasks.size(); ++t) {  // inputs are originals or earlier tasks
+        uint64_t sum = 0;
+        for (int fid : P.tasks[t].inputs) sum += ub[fid];
+        ub[w.nf + t] = std::min(sum, k);
+    }
+    return ub;
+}
+
 int gpube_build_descriptors(util_state *s)
 {
     const wcsp &w = *s->w;
     Plan &P = s->plan;
     const DescLayout &D = layout_of(s);
     const size_t nt = P.tasks.size();
+    const std::vector<uint64_t> ub = upper_bounds(s);
     const int NT = s->cfg.threads;
     const size_t blob_bytes = s->value_off + s->value_bytes - s->desc_off;
     s->host_blob.assign(blob_bytes, 0);
@@ -547,6 +575,9 @@ int gpube_build_descriptors(util_state *s)
         x.n_uo = T.n_uo;
         // a row of the cp.async path sums 2 + (F - n_uo) terms, each <= top_k
         x.lazy = (static_cast<uint64_t>(2 + x.F - T.n_uo) * w.top_k <= 0xFFFFFFFFull) ? 1 : 0;
+        uint64_t sum_ub = 0;
+        for (int fid : T.inputs) sum_ub += ub[fid];
+        x.nosat = (w.cost_type == WCSP_INT32_SAT && sum_ub < w.top_k && sum_ub < (1ull << 30)) ? 1 : 0;
         for (size_t f = 0; f < T.inputs.size(); ++f) {
             InDev &in = ind[in_pos + f];
             in.ptr = func_ptr(s, T.inputs[f]);

@@ -484,7 +484,12 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
 // clamped entry equals k and the first argmin is 0.
 // U > 0: the radix R0 of u is U (rows unrolled, the per-u partial sums held
 // in registers); U = 0: any R0 <= 4 (partial sums read from shared memory).
-template <typename C, int D, int NRG, bool FOLD, int U = 0>
+// PK (integer costs whose sums stay below the top cost and 2^30, D <= 4): the
+// partial sums are kept as keys (s << 2 | l) and the group run as (x << 2),
+// so a row's sums are D adds of keys, its minimum and first argmin one
+// unsigned min over them (equal sums: the lower l has the lower key), and no
+// saturation is needed.
+template <typename C, int D, int NRG, bool FOLD, int U = 0, bool PK = false>
 __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const unsigned char *stage, unsigned char *pipe,
                                           const int32_t *arows, int lo, int g0, int g1, uint32_t k)
 {
@@ -492,6 +497,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     using T = typename C::val;
     using A = typename C::acc;
     constexpr bool kInt = std::is_same<T, int32_t>::value;
+    static_assert(!PK || (kInt && FOLD && NRG == 0 && U > 0 && D <= 4), "packed keys: integer rows of two terms");
     constexpr int FC = 3, SA = 4, SB = 4, UMAX = 4;
     constexpr int R = NRG > 0 ? NRG : 1;
     constexpr int CH = (D % 4 == 0) ? 16 : (D % 2 == 0) ? 8 : 4;  // bytes per copy
@@ -533,6 +539,12 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
         if constexpr (U > 0) {
 #pragma unroll
             for (int u = 0; u < U; ++u) slot_load<D, CH>(bus_s + static_cast<uint32_t>(u * NCH * NT * CH), NT, tid, bur[u]);
+        }
+        if constexpr (PK) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int l = 0; l < D; ++l) bur[u][l] = (bur[u][l] << 2) | static_cast<uint32_t>(l);
         }
     }
     const int gf = nlo;  // the group input
@@ -620,7 +632,21 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
                 if (f == rg0 + r) ro[r] = a[1 + f];
         }
         int32_t o = a[0] + lo;
-        if constexpr (FOLD) {
+        if constexpr (PK) {
+            uint32_t xs[D];
+#pragma unroll
+            for (int l = 0; l < D; ++l) xs[l] = static_cast<uint32_t>(x[l]) << 2;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                uint32_t m = bur[u][0] + xs[0];
+#pragma unroll
+                for (int l = 1; l < D; ++l) m = min(m, bur[u][l] + xs[l]);
+                out[o] = static_cast<T>(m >> 2);
+                arg[o] = static_cast<uint8_t>(m & 3u);
+                o += d0;
+            }
+            issue(g + kPipe, slot);  // the slot's data has been consumed
+        } else if constexpr (FOLD) {
 #pragma unroll
             for (int u = 0; u < (U ? U : UMAX); ++u)
                 if (U || u < R0) {
@@ -663,6 +689,14 @@ __device__ __forceinline__ void item_fixed(const TaskDev *__restrict__ tkp, cons
             if (tk.R0 <= 4) {
                 switch (tk.F - tk.n_uo) {
                 case 0:  // the radix of u as a template constant: unrolled rows, partial sums in registers
+                    if constexpr (std::is_same<C, Cost<int32_t>>::value && D <= 4) {
+                        if (tk.nosat && tk.R0 >= 2) {  // sums below the top cost: packed keys
+                            if (tk.R0 == 4) item_pipe<C, D, 0, true, 4, true>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                            else if (tk.R0 == 3) item_pipe<C, D, 0, true, 3, true>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                            else item_pipe<C, D, 0, true, 2, true>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                            break;
+                        }
+                    }
                     if (tk.R0 == 4) item_pipe<C, D, 0, true, 4>(tkp, stage, pipe, arows, lo, g0, g1, k);
                     else if (tk.R0 == 3) item_pipe<C, D, 0, true, 3>(tkp, stage, pipe, arows, lo, g0, g1, k);
                     else if (tk.R0 == 2) item_pipe<C, D, 0, true, 2>(tkp, stage, pipe, arows, lo, g0, g1, k);

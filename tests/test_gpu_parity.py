@@ -304,3 +304,19 @@ def test_paper_random_network_d100(orc):
     st, res = run_state(inst, "be", order="given", order_array=o)
     check_tables(inst, st, run)
     assert res.bound == run.bound == res.cost
+
+
+@pytest.mark.parametrize("hi,top_k", [(1000, 1 << 30), (1000, 20000), (1000, 9000), (1 << 26, (1 << 31) - 1)])
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_grid_rows_below_and_at_the_top_cost(orc, d, hi, top_k):
+    # the pipelined grid rows take packed (sum << 2 | l) keys when every sum
+    # stays below the top cost and 2^30, and the saturating rows otherwise
+    # (sums reaching k, or sums above 2^30 with k = 2^31 - 1): both against
+    # the oracle, bit for bit
+    inst = synth.grid_wcsp(5, 8, d, seed=d, lo=0, hi=hi, unary=False, top_k=top_k)
+    o = np.arange(inst.n, dtype=np.int32)
+    run = orc.eliminate(inst, o, "be")
+    for kw in (dict(), dict(use_graph=True, block_threads=128, rows_per_item=16)):
+        st, res = run_state(inst, "be", order="natural", **kw)
+        check_tables(inst, st, run)
+        assert res.bound == run.bound and list(res.assignment) == list(run.sigma)
