@@ -608,19 +608,19 @@ int gpube_build_descriptors(util_state *s)
         L.tasks = td_dev + first;
         L.prefix = pre_dev + pp;
         L.n_tasks = count;
-        int smem = 0, pipe_d = 0;
+        int smem = 0, pipe_b = 0;
         double work = 0.0;  // thread-rows of the launch, idle lanes of partial lo chunks included
         for (int i = 0; i < count; ++i) {
             const TaskDev &x = td[first + i];
             smem = std::max(smem, x.stage_bytes);
-            if (x.pipe) pipe_d = std::max(pipe_d, x.d);
+            if (x.pipe) pipe_b = std::max(pipe_b, pipe_bytes_per_thread(x.d));
             work += static_cast<double>(x.nlc) * NT * x.G * x.R0;
         }
         // shared memory: staged tables | the item's A rows | pipeline slots
         // and four per-u partial sums per thread (cp.async path)
         L.arows_off = static_cast<int32_t>(al(smem, 16));
-        L.pipe_off = L.arows_off + (pipe_d ? kMaxPipeRows * 16 : 0);
-        if (pipe_d) smem = L.pipe_off + kPipe * NT * pipe_d * 4 + 4 * NT * pipe_d * 4;
+        L.pipe_off = L.arows_off + (pipe_b ? kMaxPipeRows * 16 : 0);
+        if (pipe_b) smem = L.pipe_off + NT * pipe_b;
         const int64_t cap = static_cast<int64_t>(blocks_per_sm(smem)) * s->num_sms;
         // whole waves: items of about equal size, about a multiple of the
         // resident CTAs, near rows_per_item rows per thread

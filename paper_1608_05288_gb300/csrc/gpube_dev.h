@@ -83,7 +83,12 @@ struct alignas(16) TaskDev {
 // and the most groups one item of that path spans (its A rows are copied to
 // shared memory, 16 bytes each).
 constexpr int kPipe = 4;
+constexpr int kPipeSmall = 8;  // the depth for runs of at most 16 bytes (d <= 4)
 constexpr int kMaxPipeRows = 256;
+// Pipeline depth and shared-memory bytes per thread of the cp.async path for
+// domain d: the slots plus four per-u partial sums, 4d bytes each.
+constexpr int pipe_depth(int d) { return d <= 4 ? kPipeSmall : kPipe; }
+constexpr int pipe_bytes_per_thread(int d) { return (pipe_depth(d) + 4) * 4 * d; }
 
 // One kernel launch: a list of tasks whose work items are handed out by an
 // atomic counter (a device-side work queue).

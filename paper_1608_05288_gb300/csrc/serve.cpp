@@ -299,7 +299,7 @@ extern "C" int srv_step(gpube_server *s)
     if (!keys.empty()) key = keys[static_cast<size_t>(s->key_turn++) % keys.size()];
     std::vector<TaskDev> tds;
     std::vector<Request *> finishing;
-    int smem = 0, pipe_d = 0;
+    int smem = 0, pipe_b = 0;
     for (Request *r : s->active) {
         if (r->state != kActive) continue;
         if (!r->up_waited) {
@@ -313,7 +313,7 @@ extern "C" int srv_step(gpube_server *s)
             for (int i = P.level_off[r->next_level]; i < P.level_off[r->next_level + 1]; ++i) {
                 tds.push_back(td[i]);
                 smem = std::max(smem, td[i].stage_bytes);
-                if (td[i].pipe) pipe_d = std::max(pipe_d, td[i].d);
+                if (td[i].pipe) pipe_b = std::max(pipe_b, pipe_bytes_per_thread(td[i].d));
             }
             r->next_level++;
         }
@@ -352,8 +352,8 @@ extern "C" int srv_step(gpube_server *s)
         L.status = s->work + 2;
         L.top_k = key.second;
         L.arows_off = static_cast<int32_t>(al(smem, 16));
-        L.pipe_off = L.arows_off + (pipe_d ? kMaxPipeRows * 16 : 0);
-        if (pipe_d) smem = L.pipe_off + kPipe * s->threads * pipe_d * 4 + 4 * s->threads * pipe_d * 4;
+        L.pipe_off = L.arows_off + (pipe_b ? kMaxPipeRows * 16 : 0);
+        if (pipe_b) smem = L.pipe_off + s->threads * pipe_b;
         SRV_TRY(cudaMemsetAsync(L.counter, 0, 4, s->stream));
         const int64_t cap = static_cast<int64_t>(util_max_blocks_per_sm(key.first, s->threads, smem)) * s->num_sms;
         const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(tot, cap)));

@@ -471,9 +471,9 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
 }
 
 // Same item, when exactly one input is a group input and lives in global
-// memory (the usual large child bucket function): its run for group g + kPipe
+// memory (the usual large child bucket function): its run for group g + KP
 // is copied to this thread's shared-memory slot by cp.async while group g is
-// processed, so kPipe loads per thread are in flight without holding
+// processed, so KP loads per thread are in flight without holding
 // registers.  Slot layout [slot][chunk][thread] keeps the reads conflict-free.
 //
 // FOLD (R0 <= 4): the inputs whose only hi digit is u are added, once per
@@ -502,6 +502,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     constexpr int R = NRG > 0 ? NRG : 1;
     constexpr int CH = (D % 4 == 0) ? 16 : (D % 2 == 0) ? 8 : 4;  // bytes per copy
     constexpr int NCH = D * 4 / CH;                                  // copies per run
+    constexpr int KP = D <= 4 ? kPipeSmall : kPipe;                  // groups in flight (pipe_depth(D))
     const int NT = blockDim.x, tid = threadIdx.x;
     const int nlo = tk.n_lo, ngi = tk.n_gi, R0 = tk.R0;
     const int rg0 = FOLD ? tk.n_uo : ngi;  // first general per-row input
@@ -520,7 +521,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     // the slots' A rows, and the per-u partial sums, each laid out
     // [index][chunk][thread] so that the 16-byte reads are conflict-free
     const uint32_t pipe_s = smem_addr(pipe);
-    const uint32_t bus_s = pipe_s + static_cast<uint32_t>(kPipe * NCH * NT * CH);
+    const uint32_t bus_s = pipe_s + static_cast<uint32_t>(KP * NCH * NT * CH);
     const uint32_t arows_s = smem_addr(arows);
     A bur[U ? U : 1][D];
     if constexpr (FOLD) {
@@ -615,10 +616,10 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
         arg[o] = static_cast<uint8_t>(bi);
     };
 #pragma unroll
-    for (int s = 0; s < kPipe; ++s) issue(g0 + s, s);
+    for (int s = 0; s < KP; ++s) issue(g0 + s, s);
     int slot = 0;
     for (int g = g0; g < g1; ++g) {
-        cp_async_wait<kPipe - 1>();
+        cp_async_wait<KP - 1>();
         int32_t a[SA];
         lds_int4(arows_s + static_cast<uint32_t>((g - g0) * SA * 4), a);
         T x[D];
@@ -645,7 +646,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
                 arg[o] = static_cast<uint8_t>(m & 3u);
                 o += d0;
             }
-            issue(g + kPipe, slot);  // the slot's data has been consumed
+            issue(g + KP, slot);  // the slot's data has been consumed
         } else if constexpr (FOLD) {
 #pragma unroll
             for (int u = 0; u < (U ? U : UMAX); ++u)
@@ -660,12 +661,12 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
                     row(bu, x, ro, o);
                     o += d0;
                 }
-            issue(g + kPipe, slot);  // the slot's data has been consumed
+            issue(g + KP, slot);  // the slot's data has been consumed
         } else {
             A pre[D];
 #pragma unroll
             for (int l = 0; l < D; ++l) pre[l] = C::add(base[l], x[l], k);
-            issue(g + kPipe, slot);
+            issue(g + KP, slot);
             T zero[D];
 #pragma unroll
             for (int l = 0; l < D; ++l) zero[l] = T(0);
@@ -674,7 +675,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
                 o += d0;
             }
         }
-        slot = (slot + 1 == kPipe) ? 0 : slot + 1;
+        slot = (slot + 1 == KP) ? 0 : slot + 1;
     }
     cp_async_wait<0>();
 }
