@@ -144,7 +144,9 @@ typedef struct solve_result {
     int32_t n_levels;       /* elimination-tree levels                              */
     int32_t n_launches;     /* UTIL kernel launches of one run                      */
     int64_t util_entries;   /* sum over tasks of separator rows x |D_x| (joint rows) */
-    int64_t alg_bytes;      /* 4 x input entries + 5 x output entries, over tasks   */
+    int64_t alg_bytes;      /* 4 x input entries + 5 x output entries, over tasks
+                               (4 x output entries for the sum-product kinds, which
+                               write no argmin tables)                              */
     double plan_ms;         /* host planning time                                   */
     double util_ms;         /* device time of the UTIL phase (CUDA events)          */
     double value_ms;        /* device time of the VALUE phase                       */
@@ -216,7 +218,8 @@ int mbe_solve(wcsp *w, int32_t i_bound, const solve_opts *opts, solve_result *re
  * A variable in no function contributes a factor |D| to Z.  With mini-buckets
  * the bound is a lower bound on -log Z (each mini-bucket summed on its own
  * can only enlarge Z).  There is no value phase: res->cost is NaN and
- * res->assignment is not written.  +inf means Z = 0. */
+ * res->assignment is not written, and no argmin tables are written.  +inf
+ * means Z = 0. */
 int logz_solve(wcsp *w, int32_t i_bound, const solve_opts *opts, solve_result *res);
 
 /* DPOP UTIL phase (Section 4.1) along the pseudo-tree parent[] (host, n

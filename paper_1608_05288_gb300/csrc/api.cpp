@@ -440,7 +440,7 @@ extern "C" int util_plan_info(const util_state *s, gpube_plan_info *info)
     info->util_entries = P.util_entries;
     info->out_entries = P.out_entries;
     info->in_entries = P.in_entries;
-    info->alg_bytes = 4 * P.in_entries + 5 * P.out_entries;
+    info->alg_bytes = alg_bytes_of(P);
     info->arena_bytes = s->arena_bytes;
     info->peak_live_bytes = P.peak_live_bytes;
     info->max_sep = P.width;
@@ -965,7 +965,7 @@ static void fill_stats(const util_state *s, solve_result *res)
     res->n_levels = P.n_levels;
     res->n_launches = static_cast<int32_t>(s->launches.size());
     res->util_entries = P.util_entries;
-    res->alg_bytes = 4 * P.in_entries + 5 * P.out_entries;
+    res->alg_bytes = alg_bytes_of(P);
     res->plan_ms = s->plan_ms;
 }
 

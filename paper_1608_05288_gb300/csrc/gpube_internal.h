@@ -100,6 +100,14 @@ struct Plan {
     ValuePlanH value;
 };
 
+// Algorithmic bytes of a plan: every input entry read once (4 bytes), every
+// output entry written once (4 bytes) with its argmin (1 byte; the
+// sum-product kinds write no argmin).
+inline int64_t alg_bytes_of(const Plan &P)
+{
+    return 4 * P.in_entries + (kind_sum(P.kind) ? 4 : 5) * P.out_entries;
+}
+
 // Launch parameters of one run.
 struct LaunchCfg {
     int32_t threads = 256;

@@ -257,7 +257,7 @@ static int retire(gpube_server *s)
             r->res.n_tasks = static_cast<int32_t>(P.tasks.size());
             r->res.n_levels = P.n_levels;
             r->res.util_entries = P.util_entries;
-            r->res.alg_bytes = 4 * P.in_entries + 5 * P.out_entries;
+            r->res.alg_bytes = alg_bytes_of(P);
             r->res.plan_ms = r->st->plan_ms;
             r->rc = status ? GPUBE_ETIMEDOUT : GPUBE_OK;
             r->state = status ? kFailed : kDone;

@@ -154,12 +154,15 @@ template <> struct Cost<float> {
 
 // Sum-product in the -log domain (weighted counting, partition function):
 // the terms add as fp32 -log weights, and x_i is eliminated by
-// -log sum_l exp(-s_l) instead of min_l s_l.  The argmin is still recorded.
+// -log sum_l exp(-s_l) instead of min_l s_l.  No argmin is written.
 struct SumProduct : Cost<float> {
     static constexpr bool kSum = true;
 };
 
 constexpr float kInfF = __builtin_huge_valf();
+// Factored sum-product rows below this sum of products are recomputed from
+// their raw terms (fp32 keeps full relative precision well above it).
+constexpr float kSfTiny = 1e-20f;
 
 // Elimination of one row's D sums: the first minimum and its index; for the
 // sum-product, -log sum exp(-acc[l]) taken relative to that minimum (every
@@ -356,7 +359,7 @@ __device__ __noinline__ void item_fixed_anyF(const TaskDev *__restrict__ tkp, co
             const A best = reduce_run<C, D>(acc, bi);
             const int o = Ar[0] + u * du[0] + lo;
             out[o] = C::store(best);
-            tk.arg[o] = static_cast<uint8_t>(bi);
+            if constexpr (!C::kSum) tk.arg[o] = static_cast<uint8_t>(bi);
         }
     }
 }
@@ -462,7 +465,7 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
                     int bi;
                     const A best = reduce_run<C, D>(acc, bi);
                     out[oo[j]] = C::store(best);
-                    arg[oo[j]] = static_cast<uint8_t>(bi);
+                    if constexpr (!C::kSum) arg[oo[j]] = static_cast<uint8_t>(bi);
                     oo[j] += d0;
                 }
             }
@@ -524,6 +527,15 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     const uint32_t bus_s = pipe_s + static_cast<uint32_t>(KP * NCH * NT * CH);
     const uint32_t arows_s = smem_addr(arows);
     A bur[U ? U : 1][D];
+    // SF: sum-product rows of two terms with the radix of u fixed.  Because
+    // exp(-(b_l + x_l)) = exp(-b_l) exp(-x_l), each partial sum b (once per
+    // item) and each group run x (once per group, shared by its U rows) is
+    // turned into its minimum and the exp of its offsets from it; a row is
+    // then D multiply-adds and one log: -log sum = mb + mx - log sum_l
+    // eb_l ex_l.  When that sum is tiny (the two minima at different l, far
+    // apart; or +inf terms) the row is recomputed from the raw terms.
+    constexpr bool SF = C::kSum && FOLD && NRG == 0 && U > 0;
+    float mbu[SF ? U : 1];
     if constexpr (FOLD) {
         for (int u = 0; u < R0; ++u) {
             A bu[D];
@@ -546,6 +558,19 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
             for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int l = 0; l < D; ++l) bur[u][l] = (bur[u][l] << 2) | static_cast<uint32_t>(l);
+        }
+        if constexpr (SF) {
+            // partial sums as (minimum, exp(minimum - b_l)); the raw values stay
+            // in the shared-memory slots for the rows that need them
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float m = bur[u][0];
+#pragma unroll
+                for (int l = 1; l < D; ++l) m = fminf(m, bur[u][l]);
+                mbu[u] = m;
+#pragma unroll
+                for (int l = 0; l < D; ++l) bur[u][l] = m < kInfF ? __expf(m - bur[u][l]) : 0.f;
+            }
         }
     }
     const int gf = nlo;  // the group input
@@ -613,7 +638,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
             }
         }
         out[o] = C::store(best);
-        arg[o] = static_cast<uint8_t>(bi);
+        if constexpr (!C::kSum) arg[o] = static_cast<uint8_t>(bi);
     };
 #pragma unroll
     for (int s = 0; s < KP; ++s) issue(g0 + s, s);
@@ -633,7 +658,34 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
                 if (f == rg0 + r) ro[r] = a[1 + f];
         }
         int32_t o = a[0] + lo;
-        if constexpr (PK) {
+        if constexpr (SF) {
+            float mx = x[0];
+#pragma unroll
+            for (int l = 1; l < D; ++l) mx = fminf(mx, x[l]);
+            float ex[D];
+#pragma unroll
+            for (int l = 0; l < D; ++l) ex[l] = mx < kInfF ? __expf(mx - x[l]) : 0.f;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float t = bur[u][0] * ex[0];
+#pragma unroll
+                for (int l = 1; l < D; ++l) t = fmaf(bur[u][l], ex[l], t);
+                float h;
+                if (t >= kSfTiny) {
+                    h = (mbu[u] + mx) - __logf(t);
+                } else {
+                    A bu[D], acc[D];
+                    slot_load<D, CH>(bus_s + static_cast<uint32_t>(u * NCH * NT * CH), NT, tid, bu);
+#pragma unroll
+                    for (int l = 0; l < D; ++l) acc[l] = bu[l] + x[l];
+                    int bi;
+                    h = reduce_run<C, D>(acc, bi);
+                }
+                out[o] = h;
+                o += d0;
+            }
+            issue(g + KP, slot);  // the slot's data has been consumed
+        } else if constexpr (PK) {
             uint32_t xs[D];
 #pragma unroll
             for (int l = 0; l < D; ++l) xs[l] = static_cast<uint32_t>(x[l]) << 2;
@@ -772,7 +824,7 @@ __device__ __noinline__ void item_anyD(const TaskDev *__restrict__ tkp, const un
             if constexpr (C::kSum) best = lse_value(best, t);
             const int o = a[0] + u * du[0] + lo;
             out[o] = C::store(best);
-            tk.arg[o] = static_cast<uint8_t>(bi);
+            if constexpr (!C::kSum) tk.arg[o] = static_cast<uint8_t>(bi);
         }
     }
 }
@@ -810,7 +862,7 @@ __device__ __noinline__ void item_anyD_anyF(const TaskDev *__restrict__ tkp, con
             if constexpr (C::kSum) best = lse_value(best, t);
             const int o = Ar[0] + u * du[0] + lo;
             out[o] = C::store(best);
-            tk.arg[o] = static_cast<uint8_t>(bi);
+            if constexpr (!C::kSum) tk.arg[o] = static_cast<uint8_t>(bi);
         }
     }
 }
@@ -889,7 +941,7 @@ __device__ __noinline__ void item_wide(const TaskDev *__restrict__ tkp, const un
                 if (lane == 0) {
                     const int o = Ar[0] + u * du[0] + rlo;
                     out[o] = C::store(best);
-                    tk.arg[o] = static_cast<uint8_t>(bi);
+                    if constexpr (!C::kSum) tk.arg[o] = static_cast<uint8_t>(bi);
                 }
             }
         }

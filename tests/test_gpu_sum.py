@@ -177,3 +177,23 @@ def test_serving_mixes_kinds_and_cost_types(orc):
         else:
             assert _close(res.bound, want), (kind, inst.name)
     srv.close()
+
+
+@pytest.mark.parametrize("d", [2, 3, 4])
+@pytest.mark.parametrize("scale,p_inf", [(1.0, 0.0), (60.0, 0.0), (5.0, 0.1)])
+def test_grid_rows_factored_and_recomputed(orc, d, scale, p_inf):
+    # the pipelined grid rows multiply exp-offsets of the partial sums and of
+    # the group run; rows whose product sum is tiny (large cost scale: minima
+    # at different values, far apart) or infinite (zero weights) are
+    # recomputed from the raw terms.  Both against the oracle.
+    inst = synth.grid_mrf(5, 8, d, seed=d, scale=scale, unary=False)
+    if p_inf:
+        rng = np.random.default_rng(d)
+        for t in inst.tables:
+            t[rng.random(t.size) < p_inf] = np.inf
+    o = np.arange(inst.n, dtype=np.int32)
+    run = orc.eliminate(inst, o, "be", semiring="sum")
+    for kw in (dict(), dict(use_graph=True, block_threads=128, rows_per_item=16)):
+        st, res = run_state(inst, "sum", order="natural", **kw)
+        check_sum_tables(st, run)
+        assert _close(res.bound, run.bound)
