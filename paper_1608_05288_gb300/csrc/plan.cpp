@@ -57,8 +57,10 @@ struct Bits {
 
 // Greedy min-fill: eliminate the variable whose remaining neighbours have the
 // fewest unconnected pairs; ties: fewer remaining neighbours, then lower id.
-// Only the neighbourhood (distance <= 2) of an eliminated variable changes
-// its fill, so only that region is rescored.
+// fill[] and deg[] are kept up to date edge by edge: removing v drops, for
+// each neighbour a, the missing pairs (v, x) of a's neighbourhood; adding a
+// fill edge (a, b) removes one missing pair from every common neighbour and
+// adds to a (b) the pairs (b, x) ((a, x)) that are still missing.
 std::vector<int32_t> order_minfill(const wcsp &w, int32_t *width)
 {
     const int n = w.n;
@@ -66,41 +68,29 @@ std::vector<int32_t> order_minfill(const wcsp &w, int32_t *width)
     adj.init(n);
     for (int v = 0; v < n; ++v)
         for (int u : w.adj[v]) adj.set(v, u);
-    std::vector<uint64_t> alive(adj.words, 0);
+    const int W = adj.words;
+    std::vector<uint64_t> alive(W, 0);
     for (int v = 0; v < n; ++v) alive[v / 64] |= 1ULL << (v % 64);
+    // |N(a) \ N[b]| among alive vertices (b itself excluded)
+    auto missing_from = [&](int a, int b) {
+        const uint64_t *ra = adj.row(a), *rb = adj.row(b);
+        int64_t c = 0;
+        for (int k = 0; k < W; ++k) c += __builtin_popcountll(ra[k] & alive[k] & ~rb[k]);
+        const bool b_counted = adj.test(a, b) && ((alive[b / 64] >> (b % 64)) & 1);
+        return c - (b_counted ? 1 : 0);
+    };
     std::vector<int64_t> fill(n, 0);
     std::vector<int32_t> deg(n, 0);
-    std::vector<uint64_t> nbv(adj.words);
-    auto neighbours = [&](int v, std::vector<int> &out) {
-        out.clear();
-        const uint64_t *r = adj.row(v);
-        for (int k = 0; k < adj.words; ++k) {
-            uint64_t x = r[k] & alive[k];
-            while (x) {
-                int b = __builtin_ctzll(x);
-                out.push_back(k * 64 + b);
-                x &= x - 1;
-            }
-        }
-    };
-    std::vector<int> nb, nb2;
-    auto score = [&](int v) {
-        neighbours(v, nb2);
-        const uint64_t *r = adj.row(v);
-        int64_t missing = 0;
-        for (int a : nb2) {
-            const uint64_t *ra = adj.row(a);
-            int64_t c = 0;
-            for (int k = 0; k < adj.words; ++k) c += __builtin_popcountll(r[k] & alive[k] & ~ra[k]);
-            missing += c - 1;  // a itself is in N(v) but not in N(a)
-        }
-        fill[v] = missing / 2;
-        deg[v] = static_cast<int32_t>(nb2.size());
-    };
-    for (int v = 0; v < n; ++v) score(v);
+    for (int v = 0; v < n; ++v) {
+        int64_t m = 0;
+        for (int a : w.adj[v]) m += missing_from(v, a);  // ordered pairs (a, x), x in N(v) \ N[a]
+        fill[v] = m / 2;
+        deg[v] = static_cast<int32_t>(w.adj[v].size());
+    }
     std::vector<int32_t> order;
     order.reserve(n);
-    std::vector<char> gone(n, 0), dirty(n, 0);
+    std::vector<char> gone(n, 0);
+    std::vector<int> nb;
     int32_t wmax = 0;
     for (int t = 0; t < n; ++t) {
         int best = -1;
@@ -108,31 +98,46 @@ std::vector<int32_t> order_minfill(const wcsp &w, int32_t *width)
             if (gone[v]) continue;
             if (best < 0 || fill[v] < fill[best] || (fill[v] == fill[best] && deg[v] < deg[best])) best = v;
         }
-        neighbours(best, nb);
-        wmax = std::max<int32_t>(wmax, static_cast<int32_t>(nb.size()));
-        for (int a : nb)
-            for (int b : nb)
-                if (a != b) adj.set(a, b);
-        gone[best] = 1;
-        alive[best / 64] &= ~(1ULL << (best % 64));
-        order.push_back(best);
-        std::vector<int> touched;
-        for (int a : nb) {
-            if (!dirty[a]) {
-                dirty[a] = 1;
-                touched.push_back(a);
-            }
-            neighbours(a, nb2);
-            for (int u : nb2)
-                if (!dirty[u]) {
-                    dirty[u] = 1;
-                    touched.push_back(u);
+        nb.clear();
+        {
+            const uint64_t *r = adj.row(best);
+            for (int k = 0; k < W; ++k) {
+                uint64_t x = r[k] & alive[k];
+                while (x) {
+                    nb.push_back(k * 64 + __builtin_ctzll(x));
+                    x &= x - 1;
                 }
+            }
         }
-        for (int u : touched) {
-            score(u);
-            dirty[u] = 0;
+        wmax = std::max<int32_t>(wmax, static_cast<int32_t>(nb.size()));
+        gone[best] = 1;
+        order.push_back(best);
+        // 1. best leaves the graph
+        alive[best / 64] &= ~(1ULL << (best % 64));
+        for (int a : nb) {
+            fill[a] -= missing_from(a, best);
+            deg[a] -= 1;
         }
+        // 2. its neighbours become a clique, one fill edge at a time
+        for (size_t i = 0; i < nb.size(); ++i)
+            for (size_t j2 = i + 1; j2 < nb.size(); ++j2) {
+                const int a = nb[i], b = nb[j2];
+                if (adj.test(a, b)) continue;
+                const uint64_t *ra = adj.row(a), *rb = adj.row(b);
+                for (int k = 0; k < W; ++k) {
+                    uint64_t x = ra[k] & rb[k] & alive[k];
+                    while (x) {
+                        fill[k * 64 + __builtin_ctzll(x)] -= 1;
+                        x &= x - 1;
+                    }
+                }
+                fill[a] += missing_from(a, b);
+                fill[b] += missing_from(b, a);
+                deg[a] += 1;
+                deg[b] += 1;
+                adj.set(a, b);
+                adj.set(b, a);
+            }
     }
     if (width) *width = wmax;
     return order;

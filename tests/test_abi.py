@@ -219,3 +219,21 @@ def test_condition_validates():
     plain = gb.UtilState(inst, "be")
     with pytest.raises(gb.GpubeError):
         plain.condition({1: 0})
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_minfill_order_matches_oracle_larger_graphs(orc, seed):
+    # the planner keeps fill counts incrementally; the order must equal the
+    # oracle's plain greedy min-fill (ties: fewest neighbours, lowest id)
+    kinds = [lambda s: synth.random_network_wcsp(40, 2, (0.05, 0.1, 0.25)[s % 3], seed=s),
+             lambda s: synth.grid_wcsp(5 + s % 3, 6, 2, seed=s),
+             lambda s: synth.scale_free_wcsp(50, 2, seed=s),
+             lambda s: synth.er_wcsp(60, seed=s, n_tables=45, dmax=3)]
+    inst = kinds[seed % 4](seed)
+    o, w = orc.minfill(inst)
+    w_lib = gb.WCSP(inst)
+    try:
+        st = gb.UtilState(w_lib, "be", order="minfill")
+    except gb.GpubeError:
+        pytest.skip("tables too large to plan")
+    assert list(st.order()) == list(o)
