@@ -350,13 +350,17 @@ typedef struct gpube_server gpube_server;
 
 int srv_create(size_t budget_bytes, int32_t max_slots, void *arena, size_t arena_bytes,
                void *stream, gpube_server **out);
-/* Submit a problem: plans it (kind as in util_plan) and queues it; returns a
- * request id >= 0 or a negative status (ENOMEM when it can never fit). */
+/* Submit a problem (kind as in util_plan): copies the problem, parent[] and
+ * the options' arrays (the caller may free them right away) and queues the
+ * request for the server's planner threads, which plan requests in parallel
+ * with each other and with srv_step.  Returns a request id >= 0, or EINVAL.
+ * A request whose plan fails, or that can never fit the budget (ENOMEM),
+ * ends in that status (srv_result returns it). */
 int64_t srv_submit(gpube_server *s, wcsp *w, int32_t kind, int32_t i_bound,
                    const int32_t *parent, const solve_opts *opts);
-/* Advance the server by one iteration: admit what fits, launch one merged
- * level step, retire finished requests.  Returns the number of requests
- * still in flight or queued. */
+/* Advance the server by one iteration: take finished plans, admit what
+ * fits, launch one merged level step, retire finished requests.  Returns the
+ * number of requests still being planned, queued or in flight. */
 int srv_step(gpube_server *s);
 /* Result of a finished request: 0 with res filled (assignment copied when
  * non-NULL), EAGAIN if not finished. */

@@ -392,7 +392,7 @@ class Server:
         rid = lib().srv_submit(self.h, w.h, k, int(i_bound), _ptr(par), C.byref(o))
         if rid < 0:
             _check(int(rid))
-        self._keep[rid] = (w, par, o)
+        self._keep[rid] = w.n  # the server copied the problem and its options
         return int(rid)
 
     def step(self):
@@ -402,14 +402,14 @@ class Server:
         return rc
 
     def result(self, rid):
-        w = self._keep[rid][0]
-        sigma = np.zeros(max(w.n, 1), dtype=np.int32)
+        n = self._keep[rid]
+        sigma = np.zeros(max(n, 1), dtype=np.int32)
         r = _abi.SolveResult()
         rc = lib().srv_result(self.h, int(rid), _ptr(sigma), C.byref(r))
         if rc == EAGAIN:
             return None
         _check(rc)
-        return _result(r, sigma[: w.n])
+        return _result(r, sigma[:n])
 
     def times(self, rid):
         a, b, c = C.c_double(), C.c_double(), C.c_double()

@@ -1,10 +1,16 @@
 // Continuous-batching server for streams of WCSP / DCOP instances.
 //
-// Admission: a request is planned on submit (no GPU work); its device need
-// (the plan's arena size, from the separator sizes, i.e. the induced width)
-// is known before anything is allocated.  Requests are admitted in arrival
-// order while a slot is free and a first-fit allocator finds room for them in
-// the server's memory budget; their tables stay resident until they finish.
+// Planning: srv_submit copies the problem and queues it; a pool of planner
+// threads computes each plan (ordering, buckets, work decomposition; no GPU
+// work), so the caller's thread is not held by host planning and plans of
+// many requests are computed in parallel.  A plan's device need (its arena
+// size, from the separator sizes, i.e. the induced width) is known before
+// anything is allocated; a request that can never fit the budget fails with
+// GPUBE_ENOMEM (srv_result).
+//
+// Admission: planned requests are admitted in submission order while a slot
+// is free and a first-fit allocator finds room for them in the server's
+// memory budget; their tables stay resident until they finish.
 //
 // Batching: each server step merges, for every admitted request, the tasks
 // of its next elimination-tree level into ONE persistent UTIL launch (the
@@ -17,8 +23,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "gpube_internal.h"
@@ -81,10 +92,16 @@ struct FirstFit {
     }
 };
 
-enum { kQueued = 0, kActive = 1, kValue = 2, kDone = 3, kFailed = 4 };
+enum { kQueued = 0, kActive = 1, kValue = 2, kDone = 3, kFailed = 4, kPlanning = 5 };
 
 struct Request {
     int64_t id = 0;
+    // the submission, copied (the caller may free its arrays after submit)
+    std::unique_ptr<wcsp> prob;
+    int32_t kind = 0, i_bound = 0;
+    solve_opts opts{};
+    std::vector<int32_t> parent, order, opt_parent, ev_vars;
+    std::string err;  // planning failure message
     util_state *st = nullptr;
     size_t off = 0, bytes = 0;
     int slot = -1, next_level = 0, state = kQueued, rc = 0;
@@ -118,11 +135,48 @@ struct gpube_server {
     bool dev_used[2] = {false, false};
     int flip = 0;
     int64_t key_turn = 0;  // which group of compatible requests launches next
+    // planner pool: submitted requests wait in to_plan; finished plans (or
+    // failures) wait in planned until srv_step takes them
+    std::vector<std::thread> planners;
+    std::mutex pmu;
+    std::condition_variable pcv;
+    std::deque<Request *> to_plan;
+    std::vector<Request *> planned;
+    bool stopping = false;
+    int64_t planning = 0;  // requests submitted and not yet taken by srv_step (guarded by pmu)
     int32_t *work = nullptr;  // [0..1] counters, [2] status
     int num_sms = 0, threads = 256;
     int64_t launches = 0, max_inflight = 0;
     double t0 = 0;
 };
+
+// Planner thread: plan queued requests until the server stops.
+static void planner_loop(gpube_server *s)
+{
+    for (;;) {
+        Request *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(s->pmu);
+            s->pcv.wait(lk, [&] { return s->stopping || !s->to_plan.empty(); });
+            if (s->to_plan.empty()) return;  // stopping
+            r = s->to_plan.front();
+            s->to_plan.pop_front();
+        }
+        util_state *st = nullptr;
+        int rc = util_plan(r->prob.get(), r->kind, r->i_bound, r->parent.empty() ? nullptr : r->parent.data(),
+                           &r->opts, &st);
+        if (!rc && al(st->arena_bytes, 256) > s->budget) {
+            rc = set_error(GPUBE_ENOMEM, "request needs %zu bytes, the budget is %zu", st->arena_bytes, s->budget);
+            util_state_free(st);
+            st = nullptr;
+        }
+        std::lock_guard<std::mutex> lk(s->pmu);
+        r->st = st;
+        r->rc = rc;
+        if (rc) r->err = last_error();
+        s->planned.push_back(r);
+    }
+}
 
 extern "C" int srv_create(size_t budget_bytes, int32_t max_slots, void *arena, size_t arena_bytes, void *stream,
                           gpube_server **out)
@@ -170,6 +224,9 @@ extern "C" int srv_create(size_t budget_bytes, int32_t max_slots, void *arena, s
         return rc;
     }
     s->t0 = now_ms();
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int n_planners = static_cast<int>(std::max(1u, std::min(8u, hw > 1 ? hw - 1 : 1u)));
+    for (int i = 0; i < n_planners; ++i) s->planners.emplace_back(planner_loop, s);
     *out = s;
     return GPUBE_OK;
 }
@@ -178,26 +235,43 @@ extern "C" int64_t srv_submit(gpube_server *s, wcsp *w, int32_t kind, int32_t i_
                               const solve_opts *opts)
 {
     if (!s || !w) return set_error(GPUBE_EINVAL, "null argument");
-    solve_opts o;
+    if (kind < GPUBE_KIND_BE || kind > GPUBE_KIND_SUM_MBE) return set_error(GPUBE_EINVAL, "unknown kind %d", kind);
+    Request *r = new Request();
+    solve_opts &o = r->opts;
     if (opts) o = *opts;
     else solve_opts_init(&o);
     o.block_threads = s->threads;  // one CTA size for every merged launch
     o.batched = 1;
     o.use_graph = 0;
-    util_state *st = nullptr;
-    int rc = util_plan(w, kind, i_bound, parent, &o, &st);
-    if (rc) return rc;
-    if (al(st->arena_bytes, 256) > s->budget) {
-        util_state_free(st);
-        return set_error(GPUBE_ENOMEM, "request needs %zu bytes, the budget is %zu", st->arena_bytes, s->budget);
+    o.autotune_cache = nullptr;
+    // copies of everything the plan reads, owned by the request
+    const int n = w->n;
+    r->prob.reset(new wcsp(*w));
+    if (parent) r->parent.assign(parent, parent + n);
+    if (o.order) {
+        r->order.assign(o.order, o.order + n);
+        o.order = r->order.data();
     }
-    Request *r = new Request();
+    if (o.parent) {
+        r->opt_parent.assign(o.parent, o.parent + n);
+        o.parent = r->opt_parent.data();
+    }
+    if (o.n_evidence_vars > 0 && o.evidence_vars) {
+        r->ev_vars.assign(o.evidence_vars, o.evidence_vars + o.n_evidence_vars);
+        o.evidence_vars = r->ev_vars.data();
+    }
+    r->kind = kind;
+    r->i_bound = i_bound;
+    r->state = kPlanning;
     r->id = s->next_id++;
-    r->st = st;
-    r->bytes = st->arena_bytes;
     r->t_submit = now_ms() - s->t0;
     s->reqs[r->id] = r;
-    s->queue.push_back(r);
+    {
+        std::lock_guard<std::mutex> lk(s->pmu);
+        s->to_plan.push_back(r);
+        s->planning++;
+    }
+    s->pcv.notify_one();
     return r->id;
 }
 
@@ -278,9 +352,34 @@ static int retire(gpube_server *s)
     return GPUBE_OK;
 }
 
+// Take the finished plans: failures end their request, the others join the
+// admission queue in submission order.
+static void take_planned(gpube_server *s)
+{
+    std::vector<Request *> got;
+    {
+        std::lock_guard<std::mutex> lk(s->pmu);
+        got.swap(s->planned);
+        s->planning -= static_cast<int64_t>(got.size());
+    }
+    for (Request *r : got) {
+        if (r->rc) {
+            r->state = kFailed;
+            r->t_done = now_ms() - s->t0;
+            continue;
+        }
+        r->bytes = r->st->arena_bytes;
+        r->state = kQueued;
+        auto it = std::upper_bound(s->queue.begin(), s->queue.end(), r,
+                                   [](const Request *a, const Request *b) { return a->id < b->id; });
+        s->queue.insert(it, r);
+    }
+}
+
 extern "C" int srv_step(gpube_server *s)
 {
     if (!s) return set_error(GPUBE_EINVAL, "null server");
+    take_planned(s);
     int rc = retire(s);
     if (!rc) rc = admit(s);
     if (rc) return rc;
@@ -372,7 +471,12 @@ extern "C" int srv_step(gpube_server *s)
         SRV_TRY(cudaEventRecord(r->done_ev, s->stream));
         r->state = kValue;
     }
-    return static_cast<int>(s->queue.size() + s->active.size());
+    int64_t planning;
+    {
+        std::lock_guard<std::mutex> lk(s->pmu);
+        planning = s->planning;
+    }
+    return static_cast<int>(planning + static_cast<int64_t>(s->queue.size() + s->active.size()));
 }
 
 extern "C" int srv_result(gpube_server *s, int64_t id, int32_t *assignment, solve_result *res)
@@ -381,7 +485,9 @@ extern "C" int srv_result(gpube_server *s, int64_t id, int32_t *assignment, solv
     auto it = s->reqs.find(id);
     if (it == s->reqs.end()) return set_error(GPUBE_EINVAL, "unknown request %lld", static_cast<long long>(id));
     Request *r = it->second;
-    if (r->state == kFailed) return set_error(r->rc, "request %lld failed", static_cast<long long>(id));
+    if (r->state == kFailed)
+        return set_error(r->rc, "request %lld failed%s%s", static_cast<long long>(id), r->err.empty() ? "" : ": ",
+                         r->err.c_str());
     if (r->state != kDone) return GPUBE_EAGAIN;
     if (assignment) std::copy(r->sigma.begin(), r->sigma.end(), assignment);
     if (res) {
@@ -417,6 +523,13 @@ extern "C" int srv_stats(gpube_server *s, int64_t *launches, int64_t *peak_bytes
 extern "C" void srv_free(gpube_server *s)
 {
     if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->pmu);
+        s->stopping = true;
+        s->to_plan.clear();  // requests not planned yet are never planned
+    }
+    s->pcv.notify_all();
+    for (auto &t : s->planners) t.join();
     cudaStreamSynchronize(s->stream);
     if (s->up_stream) {
         cudaStreamSynchronize(s->up_stream);

@@ -1,6 +1,6 @@
 """Continuous-batching server: every result is the same alone and in the mix
 (bit for bit, integer DCOPs), admission respects the memory budget, and an
-instance larger than the budget is refused at submit."""
+instance larger than the budget fails with ENOMEM once planned."""
 import numpy as np
 import pytest
 
@@ -70,9 +70,29 @@ def test_budget_admission_and_refusal():
         assert got[i].bound == _alone(x).bound
     big = synth.config_instance(1, 0)  # the 12x12 grid needs gigabytes
     assert gb.UtilState(big, "be", order="best").info()["arena_bytes"] > budget
+    rid = srv.submit(big, "be", order="best")  # planned by the server's planner threads
+    for _ in range(100000):
+        if srv.step() == 0:
+            break
     with pytest.raises(gb.GpubeError) as e:
-        srv.submit(big, "be", order="best")
+        srv.result(rid)
     assert e.value.code == gb.ENOMEM
+    srv.close()
+
+
+def test_many_submissions_planned_in_parallel():
+    # a burst of submissions (planned by the pool while earlier ones run);
+    # the caller's problem objects are released right after submit
+    insts = [synth.dcop_random(300 + s, n_range=(20, 80)) for s in range(60)]
+    srv = gb.Server(2 << 30, max_slots=32)
+    ids = {}
+    for i, x in enumerate(insts):
+        w = gb.WCSP(x)
+        ids[i] = srv.submit(w, "dpop", parent=x.parent)
+        del w
+    got = _drain(srv, ids)
+    for i, x in enumerate(insts[:12]):
+        assert got[i].bound == _alone(x).bound
     srv.close()
 
 
