@@ -188,6 +188,9 @@ typedef struct util_state util_state; /* opaque, library-owned plan + tables    
  * description (bad domain, repeated scope variable, wrong table length,
  * negative cost, ...).  The caller keeps ownership of d's arrays. */
 int wcsp_load(const wcsp_desc *d, wcsp **out);
+/* Release the caller's hold on a problem (a server request still using it
+ * keeps it alive until it no longer needs it).  States made from w
+ * (util_plan and the solvers) must be freed first. */
 void wcsp_free(wcsp *w);
 const char *wcsp_last_error(void);
 void solve_opts_init(solve_opts *o);
@@ -350,8 +353,9 @@ typedef struct gpube_server gpube_server;
 
 int srv_create(size_t budget_bytes, int32_t max_slots, void *arena, size_t arena_bytes,
                void *stream, gpube_server **out);
-/* Submit a problem (kind as in util_plan): copies the problem, parent[] and
- * the options' arrays (the caller may free them right away) and queues the
+/* Submit a problem (kind as in util_plan): copies parent[] and the options'
+ * arrays, takes a reference to the problem (wcsp_free may be called right
+ * away; the problem is released once no request needs it) and queues the
  * request for the server's planner threads, which plan requests in parallel
  * with each other and with srv_step.  Returns a request id >= 0, or EINVAL.
  * A request whose plan fails, or that can never fit the budget (ENOMEM),

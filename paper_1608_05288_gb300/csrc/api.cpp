@@ -160,7 +160,7 @@ extern "C" int wcsp_load(const wcsp_desc *d, wcsp **out)
     return GPUBE_OK;
 }
 
-extern "C" void wcsp_free(wcsp *w) { delete w; }
+extern "C" void wcsp_free(wcsp *w) { wcsp_unref(w); }
 
 // ---------------------------------------------------------------- planning
 static std::vector<int32_t> row_strides(const wcsp &w, const std::vector<int32_t> &scope)
@@ -818,12 +818,11 @@ extern "C" int util_bind(util_state *s, void *arena, size_t arena_bytes, void *s
         s->base = static_cast<unsigned char *>(arena);
     }
     s->stream = static_cast<cudaStream_t>(stream);
-    for (auto &e : s->ev) CUDA_TRY(cudaEventCreate(&e));
-    CUDA_TRY(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
-    std::vector<unsigned char> orig;
-    pack_originals(s, orig);
-    if (!orig.empty())
-        CUDA_TRY(cudaMemcpyAsync(s->base, orig.data(), orig.size(), cudaMemcpyHostToDevice, s->stream));
+    // (timing events and the capture stream are created when first needed)
+    if (s->orig_blob.empty()) pack_originals(s, s->orig_blob);
+    if (!s->orig_blob.empty())
+        CUDA_TRY(cudaMemcpyAsync(s->base, s->orig_blob.data(), s->orig_blob.size(), cudaMemcpyHostToDevice, s->stream));
+    std::vector<unsigned char>().swap(s->orig_blob);  // staged by the copy; not needed again
     int rc = upload_descriptors(s);
     if (rc) return rc;
     CUDA_TRY(cudaMemsetAsync(s->base + s->status_off, 0, 8, s->stream));
@@ -835,6 +834,18 @@ extern "C" int util_bind(util_state *s, void *arena, size_t arena_bytes, void *s
                                [s->plan.tasks.size()],
                            reinterpret_cast<const int32_t *>(s->base + D.pool), s->num_sms, s->stream));
     s->bound = true;
+    return GPUBE_OK;
+}
+
+// The host copy of the original tables in their device layout, made ahead of
+// util_bind (e.g. by a planner thread; the layout does not depend on where
+// the arena is).
+void gpube_prepack(util_state *s) { pack_originals(s, s->orig_blob); }
+
+static int ensure_events(util_state *s)
+{
+    for (auto &e : s->ev)
+        if (!e) CUDA_TRY(cudaEventCreate(&e));
     return GPUBE_OK;
 }
 
@@ -853,8 +864,10 @@ int gpube_enqueue_util(util_state *s, cudaStream_t st)
 extern "C" int util_run(util_state *s)
 {
     if (!s || !s->bound) return set_error(GPUBE_EINVAL, "state is not bound");
+    if (int rc = ensure_events(s)) return rc;
     if (s->use_graph) {
         if (!s->graph) {
+            if (!s->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
             cudaGraph_t g = nullptr;
             CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
             int rc = gpube_enqueue_util(s, s->cap_stream);
@@ -885,6 +898,7 @@ extern "C" int util_value_launch(util_state *s)
 {
     if (!s || !s->bound) return set_error(GPUBE_EINVAL, "state is not bound");
     if (!s->ran) return set_error(GPUBE_EINVAL, "VALUE phase before the UTIL phase");
+    if (int rc = ensure_events(s)) return rc;
     CUDA_TRY(cudaEventRecord(s->ev[2], s->stream));
     CUDA_TRY(launch_value(s->vdev, s->ktype, s->value_smem, s->stream));
     CUDA_TRY(cudaEventRecord(s->ev[3], s->stream));
@@ -927,7 +941,10 @@ extern "C" int util_condition(util_state *s, int32_t n, const int32_t *vars, con
             for (int l = 0; l < c.dom[vars[i]]; ++l)
                 c.itab[j][l] = (a < 0 || l == a) ? 0 : static_cast<int32_t>(c.top_k);
     }
-    if (!s->bound) return GPUBE_OK;  // util_bind uploads the current tables
+    if (!s->bound) {
+        std::vector<unsigned char>().swap(s->orig_blob);  // util_bind packs the current tables
+        return GPUBE_OK;
+    }
     // the evidence tables are the last originals of the arena: one copy of
     // their span (the host buffer is staged before cudaMemcpyAsync returns)
     const Plan &P = s->plan;
@@ -950,8 +967,8 @@ extern "C" int util_last_times(util_state *s, double *util_ms, double *value_ms)
 {
     if (!s || !s->bound) return set_error(GPUBE_EINVAL, "state is not bound");
     float a = 0.f, b = 0.f;
-    if (s->ran) CUDA_TRY(cudaEventElapsedTime(&a, s->ev[0], s->ev[1]));
-    if (s->value_ran) CUDA_TRY(cudaEventElapsedTime(&b, s->ev[2], s->ev[3]));
+    if (s->ran && s->ev[1]) CUDA_TRY(cudaEventElapsedTime(&a, s->ev[0], s->ev[1]));
+    if (s->value_ran && s->ev[3]) CUDA_TRY(cudaEventElapsedTime(&b, s->ev[2], s->ev[3]));
     if (util_ms) *util_ms = a;
     if (value_ms) *value_ms = b;
     return GPUBE_OK;
@@ -991,8 +1008,8 @@ extern "C" int value_propagate(util_state *s, int32_t *assignment, solve_result 
             memcpy(res->assignment, buf.data() + 24, 4 * static_cast<size_t>(n));
         fill_stats(s, res);
         float a = 0.f, b = 0.f;
-        cudaEventElapsedTime(&a, s->ev[0], s->ev[1]);
-        cudaEventElapsedTime(&b, s->ev[2], s->ev[3]);
+        if (s->ev[1]) cudaEventElapsedTime(&a, s->ev[0], s->ev[1]);
+        if (s->ev[3]) cudaEventElapsedTime(&b, s->ev[2], s->ev[3]);
         res->util_ms = a;
         res->value_ms = b;
     }

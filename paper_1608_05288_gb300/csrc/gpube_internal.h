@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <memory>
 #include <string>
 #include <vector>
@@ -21,7 +22,23 @@ struct wcsp {
     int32_t cost_type = WCSP_INT32_SAT;
     uint32_t top_k = 1u << 30;
     std::vector<std::vector<int32_t>> adj;     // primal graph, sorted neighbour lists
+    // holders: the caller (from wcsp_load until wcsp_free) and each server
+    // request that still needs the problem; the last one deletes it
+    std::atomic<int> refs{1};
+    wcsp() = default;
+    wcsp(const wcsp &o)
+        : n(o.n), dom(o.dom), nf(o.nf), scope(o.scope), itab(o.itab), ftab(o.ftab), cost_type(o.cost_type),
+          top_k(o.top_k), adj(o.adj)
+    {
+    }
+    wcsp &operator=(const wcsp &) = delete;
 };
+
+inline void wcsp_ref(wcsp *w) { w->refs.fetch_add(1, std::memory_order_relaxed); }
+inline void wcsp_unref(wcsp *w)
+{
+    if (w && w->refs.fetch_sub(1, std::memory_order_acq_rel) == 1) delete w;
+}
 
 namespace gpube {
 
@@ -190,11 +207,13 @@ struct util_state {
     int32_t value_smem = 0;
     size_t counters_off = 0, status_off = 0, result_off = 0, sigma_off = 0;
     std::vector<unsigned char> host_blob;  // staging for uploads
+    std::vector<unsigned char> orig_blob;  // original tables in device layout, when packed before binding
     DescLayout dl;
 };
 
 // api.cpp: arena layout of a planned state, its device descriptors (into
 // host_blob), and the UTIL launches of one run on a stream.
 void gpube_layout(util_state *s);
+void gpube_prepack(util_state *s);
 int gpube_build_descriptors(util_state *s);
 int gpube_enqueue_util(util_state *s, cudaStream_t st);

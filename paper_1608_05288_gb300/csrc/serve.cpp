@@ -96,8 +96,9 @@ enum { kQueued = 0, kActive = 1, kValue = 2, kDone = 3, kFailed = 4, kPlanning =
 
 struct Request {
     int64_t id = 0;
-    // the submission, copied (the caller may free its arrays after submit)
-    std::unique_ptr<wcsp> prob;
+    // the submission: a reference to the problem, copies of the arrays (the
+    // caller may free its own right after submit)
+    wcsp *prob = nullptr;
     int32_t kind = 0, i_bound = 0;
     solve_opts opts{};
     std::vector<int32_t> parent, order, opt_parent, ev_vars;
@@ -126,10 +127,12 @@ struct gpube_server {
     std::vector<Request *> active;
     std::vector<int> free_slots;
     std::vector<unsigned char *> pinned;   // per slot: status, result, assignment
+    std::vector<cudaEvent_t> slot_up, slot_done;  // per slot: upload done, result copied
     std::vector<size_t> pinned_cap;
     int64_t next_id = 0;
     // merged launch descriptors (double buffered)
     unsigned char *dbuf[2] = {nullptr, nullptr};
+    unsigned char *hbuf[2] = {nullptr, nullptr};  // pinned host staging of dbuf
     size_t dcap[2] = {0, 0};
     cudaEvent_t dev_ev[2] = {nullptr, nullptr};
     bool dev_used[2] = {false, false};
@@ -142,6 +145,7 @@ struct gpube_server {
     std::condition_variable pcv;
     std::deque<Request *> to_plan;
     std::vector<Request *> planned;
+    std::vector<std::pair<util_state *, wcsp *>> to_free;  // finished requests' plans and problems
     bool stopping = false;
     int64_t planning = 0;  // requests submitted and not yet taken by srv_step (guarded by pmu)
     int32_t *work = nullptr;  // [0..1] counters, [2] status
@@ -157,19 +161,28 @@ static void planner_loop(gpube_server *s)
         Request *r = nullptr;
         {
             std::unique_lock<std::mutex> lk(s->pmu);
-            s->pcv.wait(lk, [&] { return s->stopping || !s->to_plan.empty(); });
+            s->pcv.wait(lk, [&] { return s->stopping || !s->to_plan.empty() || !s->to_free.empty(); });
+            if (!s->to_free.empty()) {
+                auto f = s->to_free.back();
+                s->to_free.pop_back();
+                lk.unlock();
+                util_state_free(f.first);
+                wcsp_unref(f.second);
+                continue;
+            }
             if (s->to_plan.empty()) return;  // stopping
             r = s->to_plan.front();
             s->to_plan.pop_front();
         }
         util_state *st = nullptr;
-        int rc = util_plan(r->prob.get(), r->kind, r->i_bound, r->parent.empty() ? nullptr : r->parent.data(),
+        int rc = util_plan(r->prob, r->kind, r->i_bound, r->parent.empty() ? nullptr : r->parent.data(),
                            &r->opts, &st);
         if (!rc && al(st->arena_bytes, 256) > s->budget) {
             rc = set_error(GPUBE_ENOMEM, "request needs %zu bytes, the budget is %zu", st->arena_bytes, s->budget);
             util_state_free(st);
             st = nullptr;
         }
+        if (!rc) gpube_prepack(st);  // the tables' device layout, ready for the upload at admission
         std::lock_guard<std::mutex> lk(s->pmu);
         r->st = st;
         r->rc = rc;
@@ -213,9 +226,16 @@ extern "C" int srv_create(size_t budget_bytes, int32_t max_slots, void *arena, s
     s->alloc.init(budget_bytes);
     for (int i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     s->pinned.assign(max_slots, nullptr);
+    s->slot_up.assign(max_slots, nullptr);
+    s->slot_done.assign(max_slots, nullptr);
     s->pinned_cap.assign(max_slots, 0);
     cudaError_t e = cudaStreamCreateWithFlags(&s->up_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&s->work), 64);
+    // result buffers: 16 KB per slot up front (problems of up to ~4,000 variables)
+    for (int i = 0; i < max_slots && e == cudaSuccess; ++i) {
+        e = cudaMallocHost(reinterpret_cast<void **>(&s->pinned[i]), 16384);
+        if (e == cudaSuccess) s->pinned_cap[i] = 16384;
+    }
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaEventCreateWithFlags(&s->dev_ev[b], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->work, 0, 64, s->stream);
     if (e != cudaSuccess) {
@@ -244,9 +264,13 @@ extern "C" int64_t srv_submit(gpube_server *s, wcsp *w, int32_t kind, int32_t i_
     o.batched = 1;
     o.use_graph = 0;
     o.autotune_cache = nullptr;
+    // small requests: inner row blocks of two CTAs' width keep the per-task
+    // offset tables (one row per inner row) small
+    if (o.lo_target <= 0) o.lo_target = 2 * s->threads;
     // copies of everything the plan reads, owned by the request
     const int n = w->n;
-    r->prob.reset(new wcsp(*w));
+    wcsp_ref(w);
+    r->prob = w;
     if (parent) r->parent.assign(parent, parent + n);
     if (o.order) {
         r->order.assign(o.order, o.order + n);
@@ -286,18 +310,24 @@ static int admit(gpube_server *s)
         r->slot = s->free_slots.back();
         s->free_slots.pop_back();
         const size_t need = 24 + 4 * static_cast<size_t>(std::max(r->st->w->n, 1));
-        if (s->pinned_cap[r->slot] < need) {
+        if (s->pinned_cap[r->slot] < need) {  // grown geometrically: rare
+            const size_t cap = std::max(need, 2 * s->pinned_cap[r->slot]);
             if (s->pinned[r->slot]) cudaFreeHost(s->pinned[r->slot]);
             s->pinned[r->slot] = nullptr;
-            SRV_TRY(cudaMallocHost(reinterpret_cast<void **>(&s->pinned[r->slot]), need));
-            s->pinned_cap[r->slot] = need;
+            s->pinned_cap[r->slot] = 0;
+            SRV_TRY(cudaMallocHost(reinterpret_cast<void **>(&s->pinned[r->slot]), cap));
+            s->pinned_cap[r->slot] = cap;
         }
         // uploads go to a side stream so that admission does not wait for the
         // launches in flight; the compute stream waits on them by event
         int rc = util_bind(r->st, s->base + off, r->bytes, s->up_stream);
         if (rc) return rc;
-        SRV_TRY(cudaEventCreateWithFlags(&r->up_ev, cudaEventDisableTiming));
-        SRV_TRY(cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming));
+        // the slot's events (created on the slot's first use, reused after)
+        if (!s->slot_up[r->slot]) SRV_TRY(cudaEventCreateWithFlags(&s->slot_up[r->slot], cudaEventDisableTiming));
+        if (!s->slot_done[r->slot])
+            SRV_TRY(cudaEventCreateWithFlags(&s->slot_done[r->slot], cudaEventDisableTiming));
+        r->up_ev = s->slot_up[r->slot];
+        r->done_ev = s->slot_done[r->slot];
         SRV_TRY(cudaEventRecord(r->up_ev, s->up_stream));
         r->st->stream = s->stream;  // everything after the upload runs on the compute stream
         r->state = kActive;
@@ -338,12 +368,16 @@ static int retire(gpube_server *s)
             r->t_done = now_ms() - s->t0;
             s->alloc.release(r->off, r->bytes);
             s->free_slots.push_back(r->slot);
-            cudaEventDestroy(r->up_ev);
-            cudaEventDestroy(r->done_ev);
-            r->up_ev = r->done_ev = nullptr;
+            r->up_ev = r->done_ev = nullptr;  // the slot's events, reused
             r->st->sync_on_free = false;  // its work is complete (done_ev)
-            util_state_free(r->st);
+            {
+                // freeing a plan's host structures is left to the planner threads
+                std::lock_guard<std::mutex> lk(s->pmu);
+                s->to_free.push_back({r->st, r->prob});
+            }
+            s->pcv.notify_one();
             r->st = nullptr;
+            r->prob = nullptr;
             s->active.erase(s->active.begin() + i);
         } else {
             ++i;
@@ -366,6 +400,8 @@ static void take_planned(gpube_server *s)
         if (r->rc) {
             r->state = kFailed;
             r->t_done = now_ms() - s->t0;
+            wcsp_unref(r->prob);
+            r->prob = nullptr;
             continue;
         }
         r->bytes = r->st->arena_bytes;
@@ -426,14 +462,19 @@ extern "C" int srv_step(gpube_server *s)
         const size_t bytes = al(sizeof(TaskDev) * nt, 16) + 4 * (nt + 1);
         if (s->dcap[b] < bytes) {
             if (s->dbuf[b]) cudaFree(s->dbuf[b]);
-            s->dbuf[b] = nullptr;
+            if (s->hbuf[b]) cudaFreeHost(s->hbuf[b]);
+            s->dbuf[b] = s->hbuf[b] = nullptr;
+            s->dcap[b] = 0;
             const size_t cap = std::max<size_t>(bytes * 2, 1 << 16);
             SRV_TRY(cudaMalloc(reinterpret_cast<void **>(&s->dbuf[b]), cap));
+            SRV_TRY(cudaMallocHost(reinterpret_cast<void **>(&s->hbuf[b]), cap));
             s->dcap[b] = cap;
         }
-        std::vector<unsigned char> host(bytes);
-        memcpy(host.data(), tds.data(), sizeof(TaskDev) * nt);
-        int32_t *pre = reinterpret_cast<int32_t *>(host.data() + al(sizeof(TaskDev) * nt, 16));
+        // pinned staging: the copy is queued without waiting for the stream
+        // (the buffer's previous launch has completed, dev_ev[b] above)
+        unsigned char *host = s->hbuf[b];
+        memcpy(host, tds.data(), sizeof(TaskDev) * nt);
+        int32_t *pre = reinterpret_cast<int32_t *>(host + al(sizeof(TaskDev) * nt, 16));
         int64_t tot = 0;
         for (size_t i = 0; i < nt; ++i) {
             pre[i] = static_cast<int32_t>(tot);
@@ -441,7 +482,7 @@ extern "C" int srv_step(gpube_server *s)
         }
         pre[nt] = static_cast<int32_t>(tot);
         if (tot > INT32_MAX / 2) return set_error(GPUBE_ENOMEM, "merged launch has too many work items");
-        SRV_TRY(cudaMemcpyAsync(s->dbuf[b], host.data(), bytes, cudaMemcpyHostToDevice, s->stream));
+        SRV_TRY(cudaMemcpyAsync(s->dbuf[b], host, bytes, cudaMemcpyHostToDevice, s->stream));
         LaunchDev L{};
         L.tasks = reinterpret_cast<const TaskDev *>(s->dbuf[b]);
         L.prefix = reinterpret_cast<const int32_t *>(s->dbuf[b] + al(sizeof(TaskDev) * nt, 16));
@@ -530,6 +571,10 @@ extern "C" void srv_free(gpube_server *s)
     }
     s->pcv.notify_all();
     for (auto &t : s->planners) t.join();
+    for (auto &f : s->to_free) {
+        util_state_free(f.first);
+        wcsp_unref(f.second);
+    }
     cudaStreamSynchronize(s->stream);
     if (s->up_stream) {
         cudaStreamSynchronize(s->up_stream);
@@ -537,13 +582,17 @@ extern "C" void srv_free(gpube_server *s)
     }
     for (auto &kv : s->reqs) {
         Request *r = kv.second;
-        if (r->up_ev) cudaEventDestroy(r->up_ev);
-        if (r->done_ev) cudaEventDestroy(r->done_ev);
         if (r->st) util_state_free(r->st);
+        wcsp_unref(r->prob);
         delete r;
     }
+    for (auto e : s->slot_up)
+        if (e) cudaEventDestroy(e);
+    for (auto e : s->slot_done)
+        if (e) cudaEventDestroy(e);
     for (int b = 0; b < 2; ++b) {
         if (s->dbuf[b]) cudaFree(s->dbuf[b]);
+        if (s->hbuf[b]) cudaFreeHost(s->hbuf[b]);
         if (s->dev_ev[b]) cudaEventDestroy(s->dev_ev[b]);
     }
     for (auto p : s->pinned)

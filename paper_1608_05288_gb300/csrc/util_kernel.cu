@@ -2,7 +2,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "gpube_dev.h"
 
@@ -133,13 +135,29 @@ cudaError_t launch_util(const LaunchDev &L, int ktype, int grid, int threads, in
     }
 }
 
+// Resident CTAs per SM for a launch shape, cached per (device, instantiation,
+// CTA size, shared memory): every plan and every merged server launch asks.
 int util_max_blocks_per_sm(int ktype, int threads, int smem)
 {
-    switch (ktype) {
-    case kKTypeFloat: return util_max_blocks_f32(threads, smem);
-    case kKTypeSum: return util_max_blocks_sum(threads, smem);
-    default: return util_max_blocks_i32(threads, smem);
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, ktype, threads, smem);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
     }
+    int nb;
+    switch (ktype) {
+    case kKTypeFloat: nb = util_max_blocks_f32(threads, smem); break;
+    case kKTypeSum: nb = util_max_blocks_sum(threads, smem); break;
+    default: nb = util_max_blocks_i32(threads, smem); break;
+    }
+    std::lock_guard<std::mutex> g(mu);
+    cache[key] = nb;
+    return nb;
 }
 
 cudaError_t launch_expand(const ExpandDev *tasks, const int64_t *prefix, int n_tasks, int64_t total,
