@@ -152,4 +152,11 @@ struct ValueDev {
     int32_t smem_sig;           // bytes reserved for the assignment in shared memory (16-aligned)
 };
 
+// Several VALUE phases in one launch (kernel parameter, one CTA each).
+constexpr int kMaxValueBatch = 64;
+struct ValueBatch {
+    int32_t n, pad;
+    ValueDev v[kMaxValueBatch];
+};
+
 }  // namespace gpube

@@ -150,6 +150,7 @@ int util_max_blocks_per_sm(int ktype, int threads, int smem);
 cudaError_t launch_expand(const ExpandDev *tasks, const int64_t *prefix, int n_tasks, int64_t total,
                           const int32_t *pool, int num_sms, cudaStream_t s);
 cudaError_t launch_value(const ValueDev &V, int ktype, int smem, cudaStream_t s);
+cudaError_t launch_value_batch(const ValueBatch &B, int ktype, int smem, cudaStream_t s);
 cudaError_t kernels_init_device();
 cudaError_t launch_selftest_wait(int32_t *status, unsigned long long limit_ns, cudaStream_t s);
 

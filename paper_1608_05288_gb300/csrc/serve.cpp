@@ -502,15 +502,34 @@ extern "C" int srv_step(gpube_server *s)
         s->dev_used[b] = true;
         s->launches++;
     }
-    for (Request *r : finishing) {
-        util_state *st = r->st;
-        st->ran = true;
-        SRV_TRY(launch_value(st->vdev, st->ktype, st->value_smem, s->stream));
-        const size_t need = 24 + 4 * static_cast<size_t>(std::max(st->w->n, 1));
-        SRV_TRY(cudaMemcpyAsync(s->pinned[r->slot], st->base + st->status_off, need, cudaMemcpyDeviceToHost,
-                                s->stream));
-        SRV_TRY(cudaEventRecord(r->done_ev, s->stream));
-        r->state = kValue;
+    // the VALUE phases of the requests whose last level ran: one launch per
+    // value-kernel instantiation (integer / fp32 costs), one CTA per request,
+    // then each request's result copy and completion event
+    for (int vk = 0; vk < 2; ++vk) {
+        const bool want_int = vk == 0;
+        std::vector<Request *> grp;
+        for (Request *r : finishing)
+            if ((r->st->ktype == kKTypeInt) == want_int) grp.push_back(r);
+        for (size_t a = 0; a < grp.size(); a += kMaxValueBatch) {
+            const size_t b = std::min(grp.size(), a + kMaxValueBatch);
+            ValueBatch vb{};
+            int smem = 0;
+            for (size_t i = a; i < b; ++i) {
+                vb.v[vb.n++] = grp[i]->st->vdev;
+                smem = std::max(smem, grp[i]->st->value_smem);
+                grp[i]->st->ran = true;
+            }
+            SRV_TRY(launch_value_batch(vb, want_int ? kKTypeInt : kKTypeFloat, smem, s->stream));
+            for (size_t i = a; i < b; ++i) {
+                Request *r = grp[i];
+                util_state *st = r->st;
+                const size_t need = 24 + 4 * static_cast<size_t>(std::max(st->w->n, 1));
+                SRV_TRY(cudaMemcpyAsync(s->pinned[r->slot], st->base + st->status_off, need,
+                                        cudaMemcpyDeviceToHost, s->stream));
+                SRV_TRY(cudaEventRecord(r->done_ev, s->stream));
+                r->state = kValue;
+            }
+        }
     }
     int64_t planning;
     {

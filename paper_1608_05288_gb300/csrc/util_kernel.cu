@@ -19,6 +19,8 @@ int util_max_blocks_f32(int threads, int smem);
 int util_max_blocks_sum(int threads, int smem);
 cudaError_t launch_value_i32(const ValueDev &V, int smem, cudaStream_t s);
 cudaError_t launch_value_f32(const ValueDev &V, int smem, cudaStream_t s);
+cudaError_t launch_value_batch_i32(const ValueBatch &B, int smem, cudaStream_t s);
+cudaError_t launch_value_batch_f32(const ValueBatch &B, int smem, cudaStream_t s);
 cudaError_t kernel_attrs_i32(int max_smem);
 cudaError_t kernel_attrs_f32(int max_smem);
 cudaError_t kernel_attrs_sum(int max_smem);
@@ -173,6 +175,12 @@ cudaError_t launch_expand(const ExpandDev *tasks, const int64_t *prefix, int n_t
 cudaError_t launch_value(const ValueDev &V, int ktype, int smem, cudaStream_t s)
 {
     return ktype == kKTypeInt ? launch_value_i32(V, smem, s) : launch_value_f32(V, smem, s);
+}
+
+cudaError_t launch_value_batch(const ValueBatch &B, int ktype, int smem, cudaStream_t s)
+{
+    if (B.n <= 0) return cudaSuccess;
+    return ktype == kKTypeInt ? launch_value_batch_i32(B, smem, s) : launch_value_batch_f32(B, smem, s);
 }
 
 // Once per device (current device): allow every kernel the device's largest

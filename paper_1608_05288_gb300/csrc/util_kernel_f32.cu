@@ -1,5 +1,6 @@
 // Instantiation of the UTIL and VALUE kernels for fp32 -log p costs (Section 3).
 #include "util_kernel.cuh"
+#include "value_kernel.cuh"
 
 namespace gpube {
 
@@ -24,6 +25,12 @@ cudaError_t launch_value_f32(const ValueDev &V, int smem, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_value_batch_f32(const ValueBatch &B, int smem, cudaStream_t s)
+{
+    value_kernel_batch<float><<<B.n, 256, smem, s>>>(B);
+    return cudaGetLastError();
+}
+
 // Raise the dynamic shared-memory limit of this type's kernels to the
 // device maximum, once per device, outside any stream capture.
 cudaError_t kernel_attrs_f32(int max_smem)
@@ -31,6 +38,8 @@ cudaError_t kernel_attrs_f32(int max_smem)
     cudaError_t e = cudaFuncSetAttribute(util_kernel<Cost<float>>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(value_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(value_kernel_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     return e;
 }
 

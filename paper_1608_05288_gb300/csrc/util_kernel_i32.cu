@@ -1,5 +1,6 @@
 // Instantiation of the UTIL and VALUE kernels for integer WCSP costs saturating at the top cost (Section 2).
 #include "util_kernel.cuh"
+#include "value_kernel.cuh"
 
 namespace gpube {
 
@@ -24,6 +25,12 @@ cudaError_t launch_value_i32(const ValueDev &V, int smem, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_value_batch_i32(const ValueBatch &B, int smem, cudaStream_t s)
+{
+    value_kernel_batch<int32_t><<<B.n, 256, smem, s>>>(B);
+    return cudaGetLastError();
+}
+
 // Raise the dynamic shared-memory limit of this type's kernels to the
 // device maximum, once per device, outside any stream capture.
 cudaError_t kernel_attrs_i32(int max_smem)
@@ -31,6 +38,8 @@ cudaError_t kernel_attrs_i32(int max_smem)
     cudaError_t e = cudaFuncSetAttribute(util_kernel<Cost<int32_t>>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(value_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(value_kernel_batch<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     return e;
 }
 
