@@ -374,27 +374,29 @@ def bucket_case(args):
     return 0
 
 
-def grid_rows_case(args, rows=3):
+def grid_rows_case(args, rows=3, sum_product=False):
     """BE on the first `rows` rows of the headline grid (same tables, natural
     order, every bucket of row 1 is a full 4^13-entry bucket), a few GB on
-    the device: the case for kernel profiles of full-size launches."""
+    the device: the case for kernel profiles of full-size launches.  With
+    sum_product: -log Z of the same rows of the 12x12 MRF."""
     import torch
     import synth
     import paper_1608_05288_gb300 as gb
     from paper_1608_05288_gb300 import _build
     _build.build()
-    inst = synth.config_instance(1, 0)
+    inst = synth.grid_mrf(12, 12, 4, seed=0, unary=False) if sum_product else synth.config_instance(1, 0)
     nv = 12 * rows
     keep = [j for j, s in enumerate(inst.scopes) if int(np.max(s)) < nv]
     sub = synth.Instance("grid12x12_rows", inst.dom[:nv].copy(), [inst.scopes[j] for j in keep],
-                         [inst.tables[j] for j in keep], "int", inst.top_k)
+                         [inst.tables[j] for j in keep], inst.cost_type, inst.top_k)
     kw = {}
     if args.threads:
         kw["block_threads"] = args.threads
     if args.rows:
         kw["rows_per_item"] = args.rows
     os.makedirs(os.path.dirname(TUNE_CACHE), exist_ok=True)
-    st = gb.UtilState(sub, "be", order="natural", use_graph=True, autotune_cache=TUNE_CACHE, **kw)
+    st = gb.UtilState(sub, "sum" if sum_product else "be", order="natural", use_graph=True,
+                      autotune_cache=TUNE_CACHE, **kw)
     st.bind()
     if not kw:
         st.autotune()
@@ -407,7 +409,7 @@ def grid_rows_case(args, rows=3):
             ms.append(st.times()[0])
     m = statistics.median(ms)
     peak, kind = _peaks()
-    print(json.dumps({"case": f"grid12x{rows}", "util_ms": m, "alg_bytes": info["alg_bytes"],
+    print(json.dumps({"case": f"{'mrf' if sum_product else 'grid'}12x{rows}", "util_ms": m, "alg_bytes": info["alg_bytes"],
                       "gbs": info["alg_bytes"] / m / 1e6, "frac": info["alg_bytes"] / m / 1e6 / peak,
                       "launches": info["n_levels"], "arena_gb": info["arena_bytes"] / 1e9}), flush=True)
     return 0
@@ -420,7 +422,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-secondary", action="store_true")
-    ap.add_argument("--case", default="", choices=["", "bucket13", "grid3", "grid12"])
+    ap.add_argument("--case", default="", choices=["", "bucket13", "grid3", "grid12", "mrf3"])
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0)
     args = ap.parse_args()
@@ -432,6 +434,8 @@ def main():
         return grid_rows_case(args, 3)
     if args.case == "grid12":
         return grid_rows_case(args, 12)
+    if args.case == "mrf3":
+        return grid_rows_case(args, 3, sum_product=True)
 
     import torch
     import torch.distributed as dist

@@ -133,7 +133,9 @@ struct LaunchCfg {
 
 // planner (plan.cpp)
 const char *last_error();
-std::vector<int32_t> order_minfill(const wcsp &w, int32_t *width);
+// Greedy min-fill order and its width; an empty order once the width would
+// exceed give_up_above.
+std::vector<int32_t> order_minfill(const wcsp &w, int32_t *width, int32_t give_up_above = INT32_MAX);
 int32_t induced_width(const wcsp &w, const std::vector<int32_t> &order);
 std::vector<int32_t> dfs_pseudotree(const wcsp &w);
 int pseudotree_order(const wcsp &w, const int32_t *parent, std::vector<int32_t> &order);

@@ -61,7 +61,7 @@ struct Bits {
 // each neighbour a, the missing pairs (v, x) of a's neighbourhood; adding a
 // fill edge (a, b) removes one missing pair from every common neighbour and
 // adds to a (b) the pairs (b, x) ((a, x)) that are still missing.
-std::vector<int32_t> order_minfill(const wcsp &w, int32_t *width)
+std::vector<int32_t> order_minfill(const wcsp &w, int32_t *width, int32_t give_up_above)
 {
     const int n = w.n;
     Bits adj;
@@ -110,6 +110,10 @@ std::vector<int32_t> order_minfill(const wcsp &w, int32_t *width)
             }
         }
         wmax = std::max<int32_t>(wmax, static_cast<int32_t>(nb.size()));
+        if (wmax > give_up_above) {  // the caller has an order at least this good
+            if (width) *width = wmax;
+            return {};
+        }
         gone[best] = 1;
         order.push_back(best);
         // 1. best leaves the graph
@@ -305,11 +309,14 @@ int build_plan(const wcsp &w, int kind, int i_bound, const int32_t *parent, cons
         std::iota(P.order.begin(), P.order.end(), 0);
         break;
     case GPUBE_ORDER_BEST: {
-        int32_t wm = 0;
-        P.order = order_minfill(w, &wm);
+        // the natural order unless min-fill is at least as good (min-fill is
+        // abandoned as soon as its width exceeds the natural order's)
         std::vector<int32_t> nat(n);
         std::iota(nat.begin(), nat.end(), 0);
-        if (induced_width(w, nat) < wm) P.order = nat;
+        const int32_t wn = induced_width(w, nat);
+        int32_t wm = 0;
+        P.order = order_minfill(w, &wm, wn);
+        if (P.order.empty()) P.order = nat;
         break;
     }
     case GPUBE_ORDER_GIVEN: {

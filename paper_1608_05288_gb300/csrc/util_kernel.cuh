@@ -383,7 +383,7 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
     constexpr int SB = (FC + 3) / 4 * 4;
     constexpr int NG = (FC <= 3 && D <= 4) ? 2 : 1;
     constexpr int R = NR > 0 ? NR : 1;
-    const int F = tk.F, nlo = tk.n_lo, ngi = tk.n_gi, R0 = tk.R0;
+    const int nlo = tk.n_lo, ngi = tk.n_gi, R0 = tk.R0;
     const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * SB;
     // lo-only inputs: summed once
     A base[D];
