@@ -573,8 +573,6 @@ int gpube_build_descriptors(util_state *s)
                      ? 1
                      : 0;
         x.n_uo = T.n_uo;
-        // a row of the cp.async path sums 2 + (F - n_uo) terms, each <= top_k
-        x.lazy = (static_cast<uint64_t>(2 + x.F - T.n_uo) * w.top_k <= 0xFFFFFFFFull) ? 1 : 0;
         uint64_t sum_ub = 0;
         for (int fid : T.inputs) sum_ub += ub[fid];
         x.nosat = (w.cost_type == WCSP_INT32_SAT && sum_ub < w.top_k && sum_ub < (1ull << 30)) ? 1 : 0;

@@ -72,11 +72,10 @@ struct alignas(16) TaskDev {
     int32_t R0;                // radix of u (1 when there is no hi digit)
     int32_t pipe;              // 1: the one group input is prefetched by cp.async
     int32_t n_uo;              // inputs [n_gi, n_uo) mention no hi digit but u
-    int32_t lazy;              // 1: a row's sum of 2 + (F - n_uo) terms cannot wrap in uint32
     int32_t nosat;             // integer costs whose row sums stay below the top cost and 2^30
                                // (from upper bounds of the inputs): no saturation, and
                                // (sum << 2 | l) fits in 32 bits
-    int32_t pad1, pad2;
+    int32_t pad0, pad1, pad2;
 };
 
 // Depth of the per-thread cp.async pipeline of group inputs (groups ahead),
