@@ -72,7 +72,7 @@ enum gpube_order_kind {
 
 enum gpube_ibound_mode {
     GPUBE_IB_SEP_VARS = 0,    /* |scope(mini-bucket) \ {x_i}| <= i_bound                 */
-    GPUBE_IB_JOINT_VARS = 1,  /* |scope(mini-bucket)| <= i_bound (Algorithm 2 line 3)     */
+    GPUBE_IB_JOINT_VARS = 1,  /* |scope(mini-bucket)| <= i_bound (the bound of Algorithm 2) */
     GPUBE_IB_LOG2_ENTRIES = 2 /* product of the mini-bucket's domains <= 2^i_bound        */
 };
 

@@ -19,8 +19,8 @@
  * Readings of points the paper leaves open (each one is a decision shared by
  * the oracle and the library; see the design notes):
  *   - bucket of a function = its first-eliminated variable (Algorithm 1
- *     line 2 says "min" in the paper's reverse numbering; the text of
- *     Section 2.1 and the worked example fix the meaning);
+ *     picks the bucket by a minimum in the paper's reverse numbering; the
+ *     text of Section 2.1 and the worked example fix the meaning);
  *   - a bucket function's scope is its separator ordered by descending
  *     elimination position, the eliminated variable last (Section 6.2);
  *   - ties in min / argmin: the first minimum by ascending domain value;
