@@ -44,3 +44,67 @@ def test_config1_grid_full_size(orc):
             assert list(res.assignment) == list(h.sigma())
     finally:
         orc.set_threads(1)
+
+
+def _fp_close(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return bool(np.all(np.abs(a - b) <= 1e-4 * (1.0 + np.abs(b))))
+
+
+def test_mrf_logz_full_size(orc):
+    # -log Z of the 12x12 MRF (d = 4, the sum-product workload of the
+    # benchmark) in its launch configuration: every bucket function and the
+    # result against the oracle's fp64 elimination, within 1e-4 (1 + |v|)
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    import bench
+    inst = synth.grid_mrf(12, 12, 4, seed=0, unary=False)
+    os.makedirs(os.path.dirname(bench.TUNE_CACHE), exist_ok=True)
+    st = gb.UtilState(inst, "sum", order="best", use_graph=True, autotune_cache=bench.TUNE_CACHE)
+    st.bind()
+    st.autotune()
+    for _ in range(2):
+        st.run()
+    res = st.value()
+    st.sync()
+    order = st.order()
+    assert res.induced_width == 12
+    orc.set_threads(orc.max_threads())
+    try:
+        with orc.Handle(inst, order, "be", semiring="sum") as h:
+            assert h.ntasks == 144
+            for t in range(h.ntasks):
+                cost, _ = st.fetch(t)
+                assert _fp_close(cost, h.task(t).out), f"task {t}"
+            assert _fp_close([res.bound], [h.bound])
+    finally:
+        orc.set_threads(1)
+
+
+def test_separable_mrf_logz_closed_form():
+    # pairwise potentials that split as a_e(x_u) + b_e(x_v) make Z a product
+    # of per-variable sums: -log Z = sum_v -log sum_x exp(-t_v(x)), t_v the
+    # sum of the terms of v's edges; at full size (12x12, d = 4), both
+    # elimination operators' closed forms
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rng = np.random.default_rng(5)
+    base = synth.grid_mrf(12, 12, 4, seed=1, unary=False)
+    t = np.zeros((base.n, 4))
+    tables = []
+    for s in base.scopes:
+        a, b = rng.uniform(0, 2, 4), rng.uniform(0, 2, 4)
+        t[s[0]] += a
+        t[s[1]] += b
+        tables.append((a[:, None] + b[None, :]).reshape(-1))
+    inst = synth.Instance("separable", base.dom, base.scopes, tables, "real", synth.TOP_K)
+    want_sum = float(np.sum(-np.log(np.exp(-t).sum(axis=1))))
+    want_min = float(np.sum(t.min(axis=1)))
+    r_sum = gb.logz_solve(inst, order="best", use_graph=True)
+    r_min = gb.be_solve(inst, order="best", use_graph=True)
+    assert _fp_close([r_sum.bound], [want_sum])
+    assert _fp_close([r_min.bound], [want_min])
