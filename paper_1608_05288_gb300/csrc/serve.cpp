@@ -10,7 +10,10 @@
 //
 // Admission: planned requests are admitted in submission order while a slot
 // is free and a first-fit allocator finds room for them in the server's
-// memory budget; their tables stay resident until they finish.
+// memory budget; their tables stay resident until they finish.  While no
+// request waits for memory, a planner thread that finds room for its request
+// also binds it (descriptors, uploads on the thread's own stream), so the
+// serving thread only merges launches and retires results.
 //
 // Batching: each server step merges, for every admitted request, the tasks
 // of its next elimination-tree level into ONE persistent UTIL launch (the
@@ -23,6 +26,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -106,6 +110,7 @@ struct Request {
     util_state *st = nullptr;
     size_t off = 0, bytes = 0;
     int slot = -1, next_level = 0, state = kQueued, rc = 0;
+    bool bound = false;  // admitted and bound by a planner thread
     double t_submit = 0, t_admit = 0, t_done = 0;
     cudaEvent_t up_ev = nullptr, done_ev = nullptr;
     bool up_waited = false;
@@ -146,6 +151,10 @@ struct gpube_server {
     std::deque<Request *> to_plan;
     std::vector<Request *> planned;
     std::vector<std::pair<util_state *, wcsp *>> to_free;  // finished requests' plans and problems
+    std::vector<cudaStream_t> planner_up;  // per planner thread: its upload stream
+    std::mutex amu;                        // guards alloc and free_slots
+    std::atomic<int64_t> waiting{0};       // requests queued for memory (planners then leave admission alone)
+    int dev = 0;
     bool stopping = false;
     int64_t planning = 0;  // requests submitted and not yet taken by srv_step (guarded by pmu)
     int32_t *work = nullptr;  // [0..1] counters, [2] status
@@ -154,9 +163,62 @@ struct gpube_server {
     double t0 = 0;
 };
 
-// Planner thread: plan queued requests until the server stops.
-static void planner_loop(gpube_server *s)
+// Bind an admitted request (memory offset and slot assigned): its result
+// buffer, descriptors and uploads (on stream up), the slot's events.
+static int bind_request(gpube_server *s, Request *r, cudaStream_t up)
 {
+    const size_t need = 24 + 4 * static_cast<size_t>(std::max(r->st->w->n, 1));
+    if (s->pinned_cap[r->slot] < need) {  // grown geometrically: rare
+        const size_t cap = std::max(need, 2 * s->pinned_cap[r->slot]);
+        if (s->pinned[r->slot]) cudaFreeHost(s->pinned[r->slot]);
+        s->pinned[r->slot] = nullptr;
+        s->pinned_cap[r->slot] = 0;
+        SRV_TRY(cudaMallocHost(reinterpret_cast<void **>(&s->pinned[r->slot]), cap));
+        s->pinned_cap[r->slot] = cap;
+    }
+    // uploads go to a side stream so that admission does not wait for the
+    // launches in flight; the compute stream waits on them by event
+    int rc = util_bind(r->st, s->base + r->off, r->bytes, up);
+    if (rc) return rc;
+    // the slot's events (created on the slot's first use, reused after)
+    if (!s->slot_up[r->slot]) SRV_TRY(cudaEventCreateWithFlags(&s->slot_up[r->slot], cudaEventDisableTiming));
+    if (!s->slot_done[r->slot]) SRV_TRY(cudaEventCreateWithFlags(&s->slot_done[r->slot], cudaEventDisableTiming));
+    r->up_ev = s->slot_up[r->slot];
+    r->done_ev = s->slot_done[r->slot];
+    SRV_TRY(cudaEventRecord(r->up_ev, up));
+    r->st->stream = s->stream;  // everything after the upload runs on the compute stream
+    r->next_level = 0;
+    r->t_admit = now_ms() - s->t0;
+    return GPUBE_OK;
+}
+
+// Memory and a slot for a request, if both are free now.
+static bool reserve(gpube_server *s, Request *r)
+{
+    std::lock_guard<std::mutex> g(s->amu);
+    if (s->free_slots.empty()) return false;
+    size_t off;
+    if (!s->alloc.alloc(r->bytes, &off)) return false;
+    r->off = off;
+    r->slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    return true;
+}
+
+static void unreserve(gpube_server *s, Request *r)
+{
+    std::lock_guard<std::mutex> g(s->amu);
+    s->alloc.release(r->off, r->bytes);
+    s->free_slots.push_back(r->slot);
+    r->slot = -1;
+}
+
+// Planner thread: plan queued requests until the server stops; bind them
+// too when nothing waits for memory and they fit now.
+static void planner_loop(gpube_server *s, int idx)
+{
+    cudaSetDevice(s->dev);
+    const cudaStream_t up = s->planner_up[idx];
     for (;;) {
         Request *r = nullptr;
         {
@@ -183,9 +245,19 @@ static void planner_loop(gpube_server *s)
             st = nullptr;
         }
         if (!rc) gpube_prepack(st);  // the tables' device layout, ready for the upload at admission
-        std::lock_guard<std::mutex> lk(s->pmu);
         r->st = st;
+        bool bound = false;
+        if (!rc && s->waiting.load() == 0) {
+            r->bytes = st->arena_bytes;
+            if (reserve(s, r)) {
+                rc = bind_request(s, r, up);
+                if (rc) unreserve(s, r);
+                else bound = true;
+            }
+        }
+        std::lock_guard<std::mutex> lk(s->pmu);
         r->rc = rc;
+        r->bound = bound;
         if (rc) r->err = last_error();
         s->planned.push_back(r);
     }
@@ -246,7 +318,16 @@ extern "C" int srv_create(size_t budget_bytes, int32_t max_slots, void *arena, s
     s->t0 = now_ms();
     const unsigned hw = std::thread::hardware_concurrency();
     const int n_planners = static_cast<int>(std::max(1u, std::min(8u, hw > 1 ? hw - 1 : 1u)));
-    for (int i = 0; i < n_planners; ++i) s->planners.emplace_back(planner_loop, s);
+    s->dev = dev;
+    s->planner_up.assign(n_planners, nullptr);
+    for (int i = 0; i < n_planners; ++i) {
+        if (cudaError_t e2 = cudaStreamCreateWithFlags(&s->planner_up[i], cudaStreamNonBlocking); e2 != cudaSuccess) {
+            int rc = cuda_error(e2, "planner stream");
+            srv_free(s);
+            return rc;
+        }
+    }
+    for (int i = 0; i < n_planners; ++i) s->planners.emplace_back(planner_loop, s, i);
     *out = s;
     return GPUBE_OK;
 }
@@ -264,6 +345,7 @@ extern "C" int64_t srv_submit(gpube_server *s, wcsp *w, int32_t kind, int32_t i_
     o.batched = 1;
     o.use_graph = 0;
     o.autotune_cache = nullptr;
+    o.device = s->dev;
     // small requests: inner row blocks of two CTAs' width keep the per-task
     // offset tables (one row per inner row) small
     if (o.lo_target <= 0) o.lo_target = 2 * s->threads;
@@ -301,40 +383,16 @@ extern "C" int64_t srv_submit(gpube_server *s, wcsp *w, int32_t kind, int32_t i_
 
 static int admit(gpube_server *s)
 {
-    while (!s->queue.empty() && !s->free_slots.empty()) {
+    while (!s->queue.empty()) {
         Request *r = s->queue.front();
-        size_t off;
-        if (!s->alloc.alloc(r->bytes, &off)) break;  // wait until memory frees up
+        if (!reserve(s, r)) break;  // wait until memory and a slot free up
         s->queue.pop_front();
-        r->off = off;
-        r->slot = s->free_slots.back();
-        s->free_slots.pop_back();
-        const size_t need = 24 + 4 * static_cast<size_t>(std::max(r->st->w->n, 1));
-        if (s->pinned_cap[r->slot] < need) {  // grown geometrically: rare
-            const size_t cap = std::max(need, 2 * s->pinned_cap[r->slot]);
-            if (s->pinned[r->slot]) cudaFreeHost(s->pinned[r->slot]);
-            s->pinned[r->slot] = nullptr;
-            s->pinned_cap[r->slot] = 0;
-            SRV_TRY(cudaMallocHost(reinterpret_cast<void **>(&s->pinned[r->slot]), cap));
-            s->pinned_cap[r->slot] = cap;
-        }
-        // uploads go to a side stream so that admission does not wait for the
-        // launches in flight; the compute stream waits on them by event
-        int rc = util_bind(r->st, s->base + off, r->bytes, s->up_stream);
+        int rc = bind_request(s, r, s->up_stream);
         if (rc) return rc;
-        // the slot's events (created on the slot's first use, reused after)
-        if (!s->slot_up[r->slot]) SRV_TRY(cudaEventCreateWithFlags(&s->slot_up[r->slot], cudaEventDisableTiming));
-        if (!s->slot_done[r->slot])
-            SRV_TRY(cudaEventCreateWithFlags(&s->slot_done[r->slot], cudaEventDisableTiming));
-        r->up_ev = s->slot_up[r->slot];
-        r->done_ev = s->slot_done[r->slot];
-        SRV_TRY(cudaEventRecord(r->up_ev, s->up_stream));
-        r->st->stream = s->stream;  // everything after the upload runs on the compute stream
         r->state = kActive;
-        r->next_level = 0;
-        r->t_admit = now_ms() - s->t0;
         s->active.push_back(r);
     }
+    s->waiting.store(static_cast<int64_t>(s->queue.size()));
     s->max_inflight = std::max<int64_t>(s->max_inflight, static_cast<int64_t>(s->active.size()));
     return GPUBE_OK;
 }
@@ -366,8 +424,11 @@ static int retire(gpube_server *s)
             r->rc = status ? GPUBE_ETIMEDOUT : GPUBE_OK;
             r->state = status ? kFailed : kDone;
             r->t_done = now_ms() - s->t0;
-            s->alloc.release(r->off, r->bytes);
-            s->free_slots.push_back(r->slot);
+            {
+                std::lock_guard<std::mutex> g(s->amu);
+                s->alloc.release(r->off, r->bytes);
+                s->free_slots.push_back(r->slot);
+            }
             r->up_ev = r->done_ev = nullptr;  // the slot's events, reused
             r->st->sync_on_free = false;  // its work is complete (done_ev)
             {
@@ -405,11 +466,18 @@ static void take_planned(gpube_server *s)
             continue;
         }
         r->bytes = r->st->arena_bytes;
+        if (r->bound) {  // admitted and bound by its planner thread
+            r->state = kActive;
+            s->active.push_back(r);
+            continue;
+        }
         r->state = kQueued;
         auto it = std::upper_bound(s->queue.begin(), s->queue.end(), r,
                                    [](const Request *a, const Request *b) { return a->id < b->id; });
         s->queue.insert(it, r);
     }
+    s->waiting.store(static_cast<int64_t>(s->queue.size()));
+    s->max_inflight = std::max<int64_t>(s->max_inflight, static_cast<int64_t>(s->active.size()));
 }
 
 extern "C" int srv_step(gpube_server *s)
@@ -575,7 +643,10 @@ extern "C" int srv_stats(gpube_server *s, int64_t *launches, int64_t *peak_bytes
 {
     if (!s) return set_error(GPUBE_EINVAL, "null server");
     if (launches) *launches = s->launches;
-    if (peak_bytes) *peak_bytes = static_cast<int64_t>(s->alloc.peak);
+    if (peak_bytes) {
+        std::lock_guard<std::mutex> g(s->amu);
+        *peak_bytes = static_cast<int64_t>(s->alloc.peak);
+    }
     if (max_inflight) *max_inflight = s->max_inflight;
     return GPUBE_OK;
 }
@@ -590,6 +661,11 @@ extern "C" void srv_free(gpube_server *s)
     }
     s->pcv.notify_all();
     for (auto &t : s->planners) t.join();
+    for (auto st_ : s->planner_up)
+        if (st_) {
+            cudaStreamSynchronize(st_);
+            cudaStreamDestroy(st_);
+        }
     for (auto &f : s->to_free) {
         util_state_free(f.first);
         wcsp_unref(f.second);
