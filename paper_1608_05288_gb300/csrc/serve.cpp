@@ -151,6 +151,7 @@ struct gpube_server {
     std::deque<Request *> to_plan;
     std::vector<Request *> planned;
     std::vector<std::pair<util_state *, wcsp *>> to_free;  // finished requests' plans and problems
+    std::deque<Request *> to_bind;         // admitted (memory and slot reserved), to be bound
     std::vector<cudaStream_t> planner_up;  // per planner thread: its upload stream
     std::mutex amu;                        // guards alloc and free_slots
     std::atomic<int64_t> waiting{0};       // requests queued for memory (planners then leave admission alone)
@@ -223,7 +224,25 @@ static void planner_loop(gpube_server *s, int idx)
         Request *r = nullptr;
         {
             std::unique_lock<std::mutex> lk(s->pmu);
-            s->pcv.wait(lk, [&] { return s->stopping || !s->to_plan.empty() || !s->to_free.empty(); });
+            s->pcv.wait(lk, [&] {
+                return s->stopping || !s->to_plan.empty() || !s->to_free.empty() || !s->to_bind.empty();
+            });
+            if (!s->to_bind.empty()) {  // admitted by the serving thread: bind it here
+                Request *b = s->to_bind.front();
+                s->to_bind.pop_front();
+                lk.unlock();
+                int brc = bind_request(s, b, up);
+                if (brc) {
+                    cudaStreamSynchronize(up);  // no copy may still land in the released memory
+                    unreserve(s, b);
+                }
+                std::lock_guard<std::mutex> lk2(s->pmu);
+                b->rc = brc;
+                b->bound = brc == 0;
+                if (brc) b->err = last_error();
+                s->planned.push_back(b);
+                continue;
+            }
             if (!s->to_free.empty()) {
                 auto f = s->to_free.back();
                 s->to_free.pop_back();
@@ -251,8 +270,12 @@ static void planner_loop(gpube_server *s, int idx)
             r->bytes = st->arena_bytes;
             if (reserve(s, r)) {
                 rc = bind_request(s, r, up);
-                if (rc) unreserve(s, r);
-                else bound = true;
+                if (rc) {
+                    cudaStreamSynchronize(up);  // no copy may still land in the released memory
+                    unreserve(s, r);
+                } else {
+                    bound = true;
+                }
             }
         }
         std::lock_guard<std::mutex> lk(s->pmu);
@@ -383,15 +406,20 @@ extern "C" int64_t srv_submit(gpube_server *s, wcsp *w, int32_t kind, int32_t i_
 
 static int admit(gpube_server *s)
 {
+    // in order: reserve memory and a slot, then hand the binding (descriptors,
+    // uploads) to the planner threads; bound requests come back through
+    // take_planned
+    int handed = 0;
     while (!s->queue.empty()) {
         Request *r = s->queue.front();
         if (!reserve(s, r)) break;  // wait until memory and a slot free up
         s->queue.pop_front();
-        int rc = bind_request(s, r, s->up_stream);
-        if (rc) return rc;
-        r->state = kActive;
-        s->active.push_back(r);
+        std::lock_guard<std::mutex> lk(s->pmu);
+        s->to_bind.push_back(r);
+        s->planning++;
+        ++handed;
     }
+    if (handed) s->pcv.notify_all();
     s->waiting.store(static_cast<int64_t>(s->queue.size()));
     s->max_inflight = std::max<int64_t>(s->max_inflight, static_cast<int64_t>(s->active.size()));
     return GPUBE_OK;
@@ -458,9 +486,14 @@ static void take_planned(gpube_server *s)
         s->planning -= static_cast<int64_t>(got.size());
     }
     for (Request *r : got) {
-        if (r->rc) {
+        if (r->rc) {  // planning or binding failed
             r->state = kFailed;
             r->t_done = now_ms() - s->t0;
+            if (r->st) {
+                r->st->sync_on_free = false;
+                util_state_free(r->st);
+                r->st = nullptr;
+            }
             wcsp_unref(r->prob);
             r->prob = nullptr;
             continue;
