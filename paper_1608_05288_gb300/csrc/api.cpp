@@ -735,6 +735,13 @@ int gpube_build_descriptors(util_state *s)
                               8 * V.vvars.size();
     vd.plan_in_smem = (vd.smem_sig + plan_bytes <= 160 * 1024) ? 1 : 0;
     s->value_smem = vd.smem_sig + (vd.plan_in_smem ? static_cast<int32_t>(plan_bytes) : 0);
+    // a chain (one variable per level, argmin lookups, two preceding domains
+    // of at most 32 value pairs) runs on one warp with its loads issued early
+    bool chain = vd.plan_in_smem && V.n_levels == w.n && w.n > 0 && s->value_smem + 4 * w.n <= 160 * 1024;
+    for (int v = 0; chain && v < w.n; ++v) chain = V.vinfo[v].mode <= 1 && w.dom[v] <= 5;
+    vd.chain = chain ? 1 : 0;
+    vd.smem_step = static_cast<int32_t>(al(s->value_smem, 16));
+    if (chain) s->value_smem = vd.smem_step + 4 * w.n;
     return GPUBE_OK;
 }
 

@@ -149,6 +149,8 @@ struct ValueDev {
     int32_t n_terms, n_vv;      // entries of terms and of vvars / vstrides
     int32_t plan_in_smem;       // 1: vinfo, terms, vvars, vstrides are copied to shared memory
     int32_t smem_sig;           // bytes reserved for the assignment in shared memory (16-aligned)
+    int32_t chain;              // 1: one variable per level, argmin lookups, domains <= 5 (one warp)
+    int32_t smem_step;          // chain: byte offset of the copy of vorder in shared memory
 };
 
 // Several VALUE phases in one launch (kernel parameter, one CTA each).

@@ -27,6 +27,89 @@ __device__ __forceinline__ long long term_index(const int32_t *vvars, const int3
     return warp_sum_ll(idx);
 }
 
+// VALUE phase of a chain (every dependency level holds one variable, each
+// read from an argmin table), run by one warp.  The variable of step j is
+// read at an index that depends on the values assigned before it; the load
+// is issued kChainAhead steps early, when the values of steps j-2 and j-1
+// are not known yet: one candidate per combination of those two values
+// (lane c holds digit c % D0 of step j-2 and c / D0 of step j-1), and step j
+// picks its candidate by a shuffle.  The dependent load latency is thus
+// spread over three steps.  The order of the steps is copied to shared memory.
+constexpr int kChainAhead = 3;
+
+__device__ __forceinline__ int warp_sum_i(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void value_chain(const ValueDev &V, const ValueVar *vinfo, const ValueTerm *terms,
+                                            const int32_t *vvars, const int32_t *vstrides, unsigned char *sig,
+                                            int32_t *order)
+{
+    const int lane = threadIdx.x & 31;
+    const int n = V.n;
+    for (int j = lane; j < n; j += 32) order[j] = V.vorder[j];
+    __syncwarp();
+    // issue the candidate load of step j (every step < j - 2 is assigned)
+    // into the slot register c; table indices fit in int32 (tables hold
+    // fewer than 2^31 entries).  Every lane loads (lanes past the candidates
+    // reload candidate 0) and nothing reads c until its step: the load stays
+    // in flight.
+    auto prefetch = [&](int j, int &c) {
+        if (j >= n) return;
+        const int v = order[j];
+        const ValueVar vi = vinfo[v];
+        if (vi.mode != 1) return;
+        const ValueTerm t = terms[vi.term_off];
+        const int pa = j >= 2 ? order[j - 2] : -1, pb = j >= 1 ? order[j - 1] : -1;
+        int base = 0, sa = 0, sb = 0;
+        for (int q = lane; q < t.nv; q += 32) {
+            const int x = vvars[t.var_off + q];
+            const int st = vstrides[t.var_off + q];
+            if (x == pa) sa = st;
+            else if (x == pb) sb = st;
+            else base += static_cast<int>(sig[x]) * st;  // assigned at a step <= j - 3
+        }
+        base = warp_sum_i(base);
+        sa = warp_sum_i(sa);
+        sb = warp_sum_i(sb);
+        const int D0 = pa >= 0 ? vinfo[pa].d : 1, D1 = pb >= 0 ? vinfo[pb].d : 1;
+        const int cand = lane < D0 * D1 ? lane : 0;
+        const int hi = (cand * ((256 + D0 - 1) / D0)) >> 8;  // cand / D0 for cand < 32, D0 <= 5
+        c = static_cast<const uint8_t *>(t.tab)[base + (cand - hi * D0) * sa + hi * sb];
+    };
+    // one register per slot, the loop unrolled by the slot count, so that a
+    // step reads only its own slot (the other two loads stay in flight)
+    // every lane writes each assigned value itself (the same value to the same
+    // address), so each lane reads back its own writes: no warp barrier that
+    // would wait for the loads in flight.  The last two values stay in
+    // registers for the pick.
+    int va = 0, vb = 0;  // values of steps j - 2 and j - 1
+    auto step = [&](int j, int &c) {
+        if (j >= n) return;
+        const int v = order[j];
+        const int pa = j >= 2 ? order[j - 2] : -1;
+        const int D0 = pa >= 0 ? vinfo[pa].d : 1;
+        const int pick = va + D0 * vb;
+        const int val = vinfo[v].mode == 1 ? __shfl_sync(0xffffffffu, c, pick) : 0;
+        sig[v] = static_cast<unsigned char>(val);
+        va = vb;
+        vb = val;
+        prefetch(j + kChainAhead, c);  // the slot is free: load the candidates of step j + 3
+    };
+    int c0 = 0, c1 = 0, c2 = 0;
+    prefetch(0, c0);
+    prefetch(1, c1);
+    prefetch(2, c2);
+    for (int j = 0; j < n; j += kChainAhead) {
+        step(j, c0);
+        step(j + 1, c1);
+        step(j + 2, c2);
+    }
+}
+
 // VALUE phase in one CTA: variables grouped by dependency level (a variable
 // depends on the other variables of its bucket, all eliminated later), one
 // warp per variable.  BE / DPOP read the stored argmin of the bucket
@@ -66,7 +149,12 @@ __device__ __forceinline__ void value_body(const ValueDev &V)
         vstrides = s_vstrides;
     }
     __syncthreads();
-    for (int lev = 0; lev < V.n_levels; ++lev) {
+    if (V.chain) {
+        if (warp == 0)
+            value_chain(V, vinfo, terms, vvars, vstrides, sig, reinterpret_cast<int32_t *>(vsm + V.smem_step));
+        __syncthreads();
+    }
+    for (int lev = 0; lev < (V.chain ? 0 : V.n_levels); ++lev) {
         const int b = V.lev_off[lev], e = V.lev_off[lev + 1];
         for (int i = b + warp; i < e; i += nw) {
             const int v = V.vorder[i];

@@ -320,3 +320,27 @@ def test_grid_rows_below_and_at_the_top_cost(orc, d, hi, top_k):
         st, res = run_state(inst, "be", order="natural", **kw)
         check_tables(inst, st, run)
         assert res.bound == run.bound and list(res.assignment) == list(run.sigma)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_chain_value_phase(orc, seed):
+    # band-structured problems in the natural order give one variable per
+    # VALUE level: the one-warp path with early candidate loads; domains
+    # 1..5 (two preceding domains give at most 25 candidates)
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(20, 60))
+    dom = rng.integers(1, 6, size=n).astype(np.int32)
+    scopes, tables = [], []
+    for v in range(n):
+        for k in range(1, int(rng.integers(1, 4)) + 1):
+            if v + k < n:
+                s = np.array([v, v + k], dtype=np.int32)
+                scopes.append(s)
+                tables.append(rng.integers(0, 50, size=int(dom[v] * dom[v + k])).astype(np.int64))
+    inst = synth.Instance(f"band{seed}", dom, scopes, tables, "int", 1 << 30)
+    o = np.arange(n, dtype=np.int32)
+    run = orc.eliminate(inst, o, "be")
+    for kw in (dict(), dict(use_graph=True)):
+        st, res = run_state(inst, "be", order="natural", **kw)
+        assert res.bound == run.bound and res.cost == run.cost
+        assert list(res.assignment) == list(run.sigma)
