@@ -65,18 +65,14 @@ class WCSP:
         F = len(inst.scopes)
         scope_off = np.zeros(F + 1, dtype=np.int32)
         tab_off = np.zeros(F + 1, dtype=np.int64)
-        for j, s in enumerate(inst.scopes):
-            scope_off[j + 1] = scope_off[j] + len(s)
-            tab_off[j + 1] = tab_off[j] + len(inst.tables[j])
-        scope = _i32(np.concatenate([np.asarray(s) for s in inst.scopes])
-                     if F and scope_off[-1] else np.zeros(1))
+        np.cumsum(np.fromiter((len(s) for s in inst.scopes), dtype=np.int32, count=F), out=scope_off[1:])
+        np.cumsum(np.fromiter((len(t) for t in inst.tables), dtype=np.int64, count=F), out=tab_off[1:])
+        scope = _i32(np.concatenate(inst.scopes) if F and scope_off[-1] else np.zeros(1))
         if self.is_int:
-            costs = (np.concatenate([np.asarray(t) for t in inst.tables]) if F else np.zeros(1))
+            costs = np.concatenate(inst.tables) if F else np.zeros(1)
             costs = np.ascontiguousarray(np.minimum(costs, 2**31 - 1), dtype=np.int32)
         else:
-            costs = np.ascontiguousarray(
-                np.concatenate([np.asarray(t) for t in inst.tables]) if F else np.zeros(1),
-                dtype=np.float32)
+            costs = np.ascontiguousarray(np.concatenate(inst.tables) if F else np.zeros(1), dtype=np.float32)
         d = _abi.WcspDesc(self.n, _ptr(dom), F, _ptr(scope_off), _ptr(scope),
                           tab_off.ctypes.data_as(_abi.i64p), costs.ctypes.data_as(C.c_void_p),
                           INT32_SAT if self.is_int else FP32_LOG,
