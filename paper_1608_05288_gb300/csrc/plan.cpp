@@ -350,6 +350,8 @@ int build_plan(const wcsp &w, int kind, int i_bound, const int32_t *parent, cons
         return s;
     };
     std::vector<std::vector<int32_t>> bucket(n);
+    P.funcs.reserve(static_cast<size_t>(w.nf) + n);
+    P.tasks.reserve(n);
     P.funcs.resize(w.nf);
     for (int j = 0; j < w.nf; ++j) {
         Func &f = P.funcs[j];
@@ -366,9 +368,10 @@ int build_plan(const wcsp &w, int kind, int i_bound, const int32_t *parent, cons
 
     // 3. Algorithm 1 / 2: buckets, partitions, bucket functions
     const bool mbe = kind_mbe(kind);
+    std::vector<char> in_union(n, 0);  // BE: variables of the bucket's single mini-bucket
     for (int t = 0; t < n; ++t) {
         const int v = P.order[t];
-        std::vector<int32_t> B = bucket[v];
+        std::vector<int32_t> &B = bucket[v];
         if (B.empty()) {
             // a variable in no function: nothing to minimise; in the sum each
             // of its values counts, a factor |D_v| of Z
@@ -381,25 +384,31 @@ int build_plan(const wcsp &w, int kind, int i_bound, const int32_t *parent, cons
             return a < b;
         });
         std::vector<std::vector<int32_t>> mb_funcs, mb_vars;  // vars kept sorted by id
-        for (int fid : B) {
+        if (!mbe) {
+            // one bucket: the union of the scopes by marks, no partition
+            mb_vars.emplace_back();
+            mb_funcs.push_back(B);
+            for (int fid : B)
+                for (int u : P.funcs[fid].scope)
+                    if (!in_union[u]) {
+                        in_union[u] = 1;
+                        mb_vars[0].push_back(u);
+                    }
+            for (int u : mb_vars[0]) in_union[u] = 0;
+            std::sort(mb_vars[0].begin(), mb_vars[0].end());
+        }
+        for (size_t k = 0; mbe && k < B.size(); ++k) {  // Algorithm 2: first fit under the bound
+            const int fid = B[k];
             std::vector<int32_t> fv = P.funcs[fid].scope;
             std::sort(fv.begin(), fv.end());
             int placed = -1;
-            if (mbe) {
-                for (size_t b = 0; b < mb_vars.size() && placed < 0; ++b) {
-                    std::vector<int32_t> u;
-                    std::set_union(mb_vars[b].begin(), mb_vars[b].end(), fv.begin(), fv.end(),
-                                   std::back_inserter(u));
-                    if (mb_fits(w, o.ibound_mode, i_bound, u)) {
-                        mb_vars[b] = u;
-                        placed = static_cast<int>(b);
-                    }
-                }
-            } else if (!mb_vars.empty()) {
+            for (size_t b = 0; b < mb_vars.size() && placed < 0; ++b) {
                 std::vector<int32_t> u;
-                std::set_union(mb_vars[0].begin(), mb_vars[0].end(), fv.begin(), fv.end(), std::back_inserter(u));
-                mb_vars[0] = u;
-                placed = 0;
+                std::set_union(mb_vars[b].begin(), mb_vars[b].end(), fv.begin(), fv.end(), std::back_inserter(u));
+                if (mb_fits(w, o.ibound_mode, i_bound, u)) {
+                    mb_vars[b] = u;
+                    placed = static_cast<int>(b);
+                }
             }
             if (placed < 0) {
                 mb_vars.push_back(fv);
