@@ -374,6 +374,55 @@ def bucket_case(args):
     return 0
 
 
+def sweep_case(args):
+    """Throughput sweep over the paper's random-network, scale-free and grid
+    workload shapes (Section 8.1 generators, exact BE in the best order,
+    graph replay, autotuned launch shape); one JSON line per instance.
+    Instances whose largest bucket exceeds 2^30 joint entries are skipped."""
+    import torch
+    import synth
+    import paper_1608_05288_gb300 as gb
+    from paper_1608_05288_gb300 import _build
+    _build.build()
+    os.makedirs(os.path.dirname(TUNE_CACHE), exist_ok=True)
+    peak, kind = _peaks()
+    cases = []
+    for n, d, p1 in ((14, 8, 0.5), (12, 16, 0.3), (10, 32, 0.4), (8, 100, 0.4)):
+        cases.append(synth.random_network_wcsp(n, d, p1, seed=1))
+    for n, d in ((150, 4), (300, 2)):
+        cases.append(synth.scale_free_wcsp(n, d, seed=1))
+    for r, c, d in ((20, 20, 2), (14, 14, 3), (9, 9, 6), (8, 8, 8), (6, 6, 16)):
+        cases.append(synth.grid_wcsp(r, c, d, seed=1, unary=False))
+    for inst in cases:
+        try:
+            st = gb.UtilState(inst, "be", order="best", use_graph=True, autotune_cache=TUNE_CACHE)
+        except gb.GpubeError:
+            print(json.dumps({"case": inst.name, "skipped": "a bucket table over 2^31 entries"}), flush=True)
+            continue
+        info = st.info()
+        big = max(t["rows"] * int(inst.dom[t["var"]]) for t in st.tasks())
+        if big > (1 << 30):
+            print(json.dumps({"case": inst.name, "skipped": f"largest bucket {big} joint entries"}), flush=True)
+            st.free()
+            continue
+        st.bind()
+        st.autotune()
+        ms = []
+        for k in range(args.warmup + args.steps):
+            st.run()
+            st.sync()
+            if k >= args.warmup:
+                ms.append(st.times()[0])
+        m = statistics.median(ms)
+        print(json.dumps({"case": inst.name, "n": inst.n, "d": int(max(inst.dom)), "width": info["induced_width"],
+                          "buckets": info["n_tasks"], "levels": info["n_levels"],
+                          "util_entries": info["util_entries"], "util_ms": m,
+                          "entries_per_s": info["util_entries"] / (m * 1e-3),
+                          "hbm_frac": info["alg_bytes"] / (m * 1e-3) / 1e9 / peak}), flush=True)
+        st.free()
+    return 0
+
+
 def grid_rows_case(args, rows=3, sum_product=False):
     """BE on the first `rows` rows of the headline grid (same tables, natural
     order, every bucket of row 1 is a full 4^13-entry bucket), a few GB on
@@ -422,7 +471,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-secondary", action="store_true")
-    ap.add_argument("--case", default="", choices=["", "bucket13", "grid3", "grid12", "mrf3"])
+    ap.add_argument("--case", default="", choices=["", "bucket13", "grid3", "grid12", "mrf3", "sweep"])
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0)
     args = ap.parse_args()
@@ -436,6 +485,8 @@ def main():
         return grid_rows_case(args, 12)
     if args.case == "mrf3":
         return grid_rows_case(args, 3, sum_product=True)
+    if args.case == "sweep":
+        return sweep_case(args)
 
     import torch
     import torch.distributed as dist

@@ -558,7 +558,10 @@ int gpube_build_descriptors(util_state *s)
         // rows_per_item counts separator rows; an item spans whole groups
         const int64_t groups = std::max<int64_t>(1, s->cfg.rows_per_item / std::max(T.R0, 1));
         x.hc = static_cast<int32_t>(std::min<int64_t>(groups, T.G));
-        x.nlc = static_cast<int32_t>((T.P_lo + NT - 1) / NT);
+        // lo chunks: NT rows (one per thread), or NT / 32 rows for wide
+        // domains (one per warp)
+        const int64_t chunk = dclass_of(T.d) == kDClassWide ? NT / 32 : NT;
+        x.nlc = static_cast<int32_t>((T.P_lo + chunk - 1) / chunk);
         const int64_t items = static_cast<int64_t>(x.nlc) * ((T.G + x.hc - 1) / x.hc);
         if (items > INT32_MAX / 2) return set_error(GPUBE_ENOMEM, "task %d has too many work items", t);
         x.n_items = static_cast<int32_t>(items);

@@ -63,7 +63,7 @@ struct alignas(16) TaskDev {
     void *out;           // [rows] int32 or float
     uint8_t *arg;        // [rows]
     int32_t F, d, sa, sb;
-    int32_t P_lo, G, hc, nlc;  // hc = groups per item; nlc = lo chunks of blockDim.x rows
+    int32_t P_lo, G, hc, nlc;  // hc = groups per item; nlc = lo chunks (blockDim.x rows, or blockDim.x / 32 for wide domains)
     int32_t variant;           // dclass * kNumFClass + fclass
     int32_t stage_bytes;       // sum of staged bytes (multiple of 16)
     int32_t n_items;           // nlc * ceil(G / hc)

@@ -331,7 +331,10 @@ __device__ __forceinline__ void load_ints(const int32_t *p, int32_t (&a)[N])
     }
 }
 
-// Fixed domain D, any number of inputs (offsets reread per input).
+// Fixed domain D, any number of inputs (offsets read from the tables per
+// input): the lo-only inputs are summed once per item, the group inputs once
+// per group, and each row adds only the inputs that mention the fastest hi
+// digit u.
 template <typename C, int D>
 __device__ __noinline__ void item_fixed_anyF(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo,
                                                 int g0, int g1, uint32_t k)
@@ -339,17 +342,35 @@ __device__ __noinline__ void item_fixed_anyF(const TaskDev *__restrict__ tkp, co
     const TaskDev tk = *tkp;
     using T = typename C::val;
     using A = typename C::acc;
-    const int F = tk.F;
+    const int F = tk.F, nlo = tk.n_lo, ngi = tk.n_gi;
     const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * tk.sb;
     const int32_t *du = tk.A + static_cast<int64_t>(tk.G) * tk.sa;
     T *out = static_cast<T *>(tk.out);
+    A base[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) base[l] = A(0);
+    for (int f = 0; f < nlo; ++f) {
+        T v[D];
+        load_run<D>(input_base<T>(tk.in[f], stage) + Brow[f], v);
+#pragma unroll
+        for (int l = 0; l < D; ++l) base[l] = C::add(base[l], v[l], k);
+    }
     for (int g = g0; g < g1; ++g) {
         const int32_t *Ar = tk.A + static_cast<int64_t>(g) * tk.sa;
+        A pre[D];
+#pragma unroll
+        for (int l = 0; l < D; ++l) pre[l] = base[l];
+        for (int f = nlo; f < ngi; ++f) {
+            T v[D];
+            load_run<D>(input_base<T>(tk.in[f], stage) + (Ar[1 + f] + Brow[f]), v);
+#pragma unroll
+            for (int l = 0; l < D; ++l) pre[l] = C::add(pre[l], v[l], k);
+        }
         for (int u = 0; u < tk.R0; ++u) {
             A acc[D];
 #pragma unroll
-            for (int l = 0; l < D; ++l) acc[l] = A(0);
-            for (int f = 0; f < F; ++f) {
+            for (int l = 0; l < D; ++l) acc[l] = pre[l];
+            for (int f = ngi; f < F; ++f) {
                 T v[D];
                 load_run<D>(input_base<T>(tk.in[f], stage) + (Ar[1 + f] + u * du[1 + f] + Brow[f]), v);
 #pragma unroll
@@ -808,17 +829,39 @@ __device__ __noinline__ void item_anyD(const TaskDev *__restrict__ tkp, const un
             A best = A(0);
             int bi = 0;
             float t = 1.f;  // sum-product only
-            for (int l = 0; l < d; ++l) {
-                A s = C::from(q[0][l]);
-#pragma unroll
-                for (int f = 1; f < FC; ++f)
-                    if (f < F) s = C::add(s, q[f][l], k);
+            auto push = [&](A s, int l) {
                 if (l == 0 || s < best) {
                     if constexpr (C::kSum) t = l == 0 ? 1.f : t * __expf(s - best) + 1.f;
                     best = s;
                     bi = l;
                 } else if constexpr (C::kSum) {
                     if (s < kInfF) t += __expf(best - s);
+                }
+            };
+            if (d % 4 == 0) {  // runs of a multiple of 4 entries are 16-byte aligned: vector loads
+                for (int l0 = 0; l0 < d; l0 += 4) {
+                    A s4[4];
+                    T v[4];
+                    load_run<4>(q[0] + l0, v);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) s4[i] = C::from(v[i]);
+#pragma unroll
+                    for (int f = 1; f < FC; ++f)
+                        if (f < F) {
+                            load_run<4>(q[f] + l0, v);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) s4[i] = C::add(s4[i], v[i], k);
+                        }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) push(s4[i], l0 + i);
+                }
+            } else {
+                for (int l = 0; l < d; ++l) {
+                    A s = C::from(q[0][l]);
+#pragma unroll
+                    for (int f = 1; f < FC; ++f)
+                        if (f < F) s = C::add(s, q[f][l], k);
+                    push(s, l);
                 }
             }
             if constexpr (C::kSum) best = lse_value(best, t);
@@ -871,7 +914,7 @@ __device__ __noinline__ void item_anyD_anyF(const TaskDev *__restrict__ tkp, con
 // holding x_i's values j, j + 32, ...; every input's run is read by one
 // coalesced warp access per 32 values, each lane keeps its first minimum and
 // the warp combines (value, index) pairs by shuffles, ties to the lower index.
-// The warp covers the 32 rows lo0 .. lo0 + 31 of its lanes in turn.
+// The warp's row is lo (a lo chunk of a wide task has one row per warp).
 template <typename C, int FC>
 __device__ __noinline__ void item_wide(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo,
                                        int g0, int g1, uint32_t k)
@@ -881,15 +924,14 @@ __device__ __noinline__ void item_wide(const TaskDev *__restrict__ tkp, const un
     using A = typename C::acc;
     constexpr int kRuns = 8;  // 8 x 32 lanes >= 255 values
     const int lane = threadIdx.x & 31;
-    const int lo0 = lo - lane;
     const int F = tk.F, d = tk.d, R0 = tk.R0;
     const int32_t *du = tk.A + static_cast<int64_t>(tk.G) * tk.sa;
     T *out = static_cast<T *>(tk.out);
     const T *p[FC > 0 ? FC : 1];
 #pragma unroll
     for (int f = 0; f < FC; ++f) p[f] = (f < F) ? input_base<T>(tk.in[f], stage) : nullptr;
-    for (int r = 0; r < 32 && lo0 + r < tk.P_lo; ++r) {
-        const int rlo = lo0 + r;
+    {
+        const int rlo = lo;
         const int32_t *Brow = tk.B + static_cast<int64_t>(rlo) * tk.sb;
         for (int g = g0; g < g1; ++g) {
             const int32_t *Ar = tk.A + static_cast<int64_t>(g) * tk.sa;
@@ -1075,10 +1117,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
             phase ^= 1u;
         }
 
-        const int lo = lc * blockDim.x + tid;
-        // one thread per row, except the wide variant: whole warps, one row at a time
+        // one thread per row, except the wide variant: one warp per row
         const bool wide = tk.variant / kNumFClass == kDClassWide;
-        if (wide ? (lo & ~31) < tk.P_lo : lo < tk.P_lo)
+        const int lo = wide ? lc * static_cast<int>(blockDim.x >> 5) + (tid >> 5) : lc * blockDim.x + tid;
+        if (lo < tk.P_lo)
             dispatch<C>(L.tasks + a, tk, stage, stage + L.pipe_off, reinterpret_cast<const int32_t *>(stage + L.arows_off),
                         lo, h0, h1, L.top_k);
 
