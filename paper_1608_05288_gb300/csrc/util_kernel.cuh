@@ -914,15 +914,17 @@ __device__ __noinline__ void item_anyD_anyF(const TaskDev *__restrict__ tkp, con
 // holding x_i's values j, j + 32, ...; every input's run is read by one
 // coalesced warp access per 32 values, each lane keeps its first minimum and
 // the warp combines (value, index) pairs by shuffles, ties to the lower index.
-// The warp's row is lo (a lo chunk of a wide task has one row per warp).
-template <typename C, int FC>
+// The warp's row is lo (a lo chunk of a wide task has one row per warp); the
+// rows of two consecutive values of u are loaded before either is reduced,
+// so that two rows' loads are in flight.  RUNS = 32-value runs per lane
+// (4: d <= 128, 8: d <= 255).
+template <typename C, int FC, int RUNS>
 __device__ __noinline__ void item_wide(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo,
                                        int g0, int g1, uint32_t k)
 {
     const TaskDev tk = *tkp;
     using T = typename C::val;
     using A = typename C::acc;
-    constexpr int kRuns = 8;  // 8 x 32 lanes >= 255 values
     const int lane = threadIdx.x & 31;
     const int F = tk.F, d = tk.d, R0 = tk.R0;
     const int32_t *du = tk.A + static_cast<int64_t>(tk.G) * tk.sa;
@@ -930,62 +932,69 @@ __device__ __noinline__ void item_wide(const TaskDev *__restrict__ tkp, const un
     const T *p[FC > 0 ? FC : 1];
 #pragma unroll
     for (int f = 0; f < FC; ++f) p[f] = (f < F) ? input_base<T>(tk.in[f], stage) : nullptr;
-    {
-        const int rlo = lo;
-        const int32_t *Brow = tk.B + static_cast<int64_t>(rlo) * tk.sb;
-        for (int g = g0; g < g1; ++g) {
-            const int32_t *Ar = tk.A + static_cast<int64_t>(g) * tk.sa;
-            for (int u = 0; u < R0; ++u) {
-                A acc[kRuns];
+    const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * tk.sb;
+    // minimum and first argmin of one row's sums (sum-product: -log sum exp),
+    // written by lane 0
+    auto finish = [&](const A (&acc)[RUNS], int o) {
+        A best = A(0);
+        int bi = -1;
 #pragma unroll
-                for (int j = 0; j < kRuns; ++j) acc[j] = A(0);
-                for (int f = 0; f < F; ++f) {
-                    const T *q = (FC > 0 && f < FC ? p[f] : input_base<T>(tk.in[f], stage)) +
-                                 (Ar[1 + f] + u * du[1 + f] + Brow[f]);
+        for (int j = 0; j < RUNS; ++j) {
+            const int l = lane + 32 * j;
+            if (l < d && (bi < 0 || acc[j] < best)) {
+                best = acc[j];
+                bi = l;
+            }
+        }
 #pragma unroll
-                    for (int j = 0; j < kRuns; ++j) {
-                        const int l = lane + 32 * j;
-                        if (l < d) acc[j] = C::add(acc[j], q[l], k);
-                    }
-                }
-                A best = A(0);
-                int bi = -1;
+        for (int s = 16; s > 0; s >>= 1) {
+            const A ob = __shfl_xor_sync(0xffffffffu, best, s);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, s);
+            if (oi >= 0 && (bi < 0 || ob < best || (!(best < ob) && oi < bi))) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if constexpr (C::kSum) {
+            // every lane now holds the row minimum: sum exp(min - s_l) over
+            // the lane's values, then over the warp
+            if (best < kInfF) {
+                float t = 0.f;
 #pragma unroll
-                for (int j = 0; j < kRuns; ++j) {
+                for (int j = 0; j < RUNS; ++j)
+                    if (lane + 32 * j < d) t += __expf(best - acc[j]);
+#pragma unroll
+                for (int s = 16; s > 0; s >>= 1) t += __shfl_xor_sync(0xffffffffu, t, s);
+                best -= __logf(t);
+            }
+        }
+        if (lane == 0) {
+            out[o] = C::store(best);
+            if constexpr (!C::kSum) tk.arg[o] = static_cast<uint8_t>(bi);
+        }
+    };
+    for (int g = g0; g < g1; ++g) {
+        const int32_t *Ar = tk.A + static_cast<int64_t>(g) * tk.sa;
+        for (int u = 0; u < R0; u += 2) {
+            const bool two = u + 1 < R0;  // uniform across the warp
+            A a0[RUNS], a1[RUNS];
+#pragma unroll
+            for (int j = 0; j < RUNS; ++j) a0[j] = a1[j] = A(0);
+            for (int f = 0; f < F; ++f) {
+                const T *q0 = (FC > 0 && f < FC ? p[f] : input_base<T>(tk.in[f], stage)) +
+                              (Ar[1 + f] + u * du[1 + f] + Brow[f]);
+                const T *q1 = q0 + du[1 + f];
+#pragma unroll
+                for (int j = 0; j < RUNS; ++j) {
                     const int l = lane + 32 * j;
-                    if (l < d && (bi < 0 || acc[j] < best)) {
-                        best = acc[j];
-                        bi = l;
+                    if (l < d) {
+                        a0[j] = C::add(a0[j], q0[l], k);
+                        if (two) a1[j] = C::add(a1[j], q1[l], k);
                     }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const A ob = __shfl_xor_sync(0xffffffffu, best, o);
-                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                    if (oi >= 0 && (bi < 0 || ob < best || (!(best < ob) && oi < bi))) {
-                        best = ob;
-                        bi = oi;
-                    }
-                }
-                if constexpr (C::kSum) {
-                    // every lane now holds the row minimum: sum exp(min - s_l)
-                    // over the lane's values, then over the warp
-                    if (best < kInfF) {
-                        float t = 0.f;
-#pragma unroll
-                        for (int j = 0; j < kRuns; ++j)
-                            if (lane + 32 * j < d) t += __expf(best - acc[j]);
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                        best -= __logf(t);
-                    }
-                }
-                if (lane == 0) {
-                    const int o = Ar[0] + u * du[0] + rlo;
-                    out[o] = C::store(best);
-                    if constexpr (!C::kSum) tk.arg[o] = static_cast<uint8_t>(bi);
                 }
             }
+            finish(a0, Ar[0] + u * du[0] + lo);
+            if (two) finish(a1, Ar[0] + (u + 1) * du[0] + lo);
         }
     }
 }
@@ -1025,9 +1034,15 @@ __device__ __forceinline__ void dispatch(const TaskDev *__restrict__ tkp, const 
     case 6: dispatch_f<C, 7>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     case 7: dispatch_f<C, 8>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     case kDClassWide:
-        if (fc == 0) item_wide<C, 3>(tkp, stage, lo, h0, h1, k);
-        else if (fc == 1) item_wide<C, 7>(tkp, stage, lo, h0, h1, k);
-        else item_wide<C, 0>(tkp, stage, lo, h0, h1, k);
+        if (tk.d <= 128) {
+            if (fc == 0) item_wide<C, 3, 4>(tkp, stage, lo, h0, h1, k);
+            else if (fc == 1) item_wide<C, 7, 4>(tkp, stage, lo, h0, h1, k);
+            else item_wide<C, 0, 4>(tkp, stage, lo, h0, h1, k);
+        } else {
+            if (fc == 0) item_wide<C, 3, 8>(tkp, stage, lo, h0, h1, k);
+            else if (fc == 1) item_wide<C, 7, 8>(tkp, stage, lo, h0, h1, k);
+            else item_wide<C, 0, 8>(tkp, stage, lo, h0, h1, k);
+        }
         break;
     default: dispatch_f<C, 0>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     }
