@@ -223,45 +223,46 @@ def secondary(torch, gb, synth, steps):
                         "gbs": info["alg_bytes"] / (m * 1e-3) / 1e9}
     # repeated mini-bucket bounds under changing evidence (the bound inside a
     # search): one plan, util_condition + graph replay per bound, against
-    # planning and binding a new state per bound
+    # planning and binding a new state per bound (direct launches, the
+    # cheaper choice for a single run); a large and a small bound
     inst = synth.config_instance(3, 0)
     rng = np.random.default_rng(0)
     ev_vars = sorted(int(v) for v in rng.choice(inst.n, size=16, replace=False))
     draws = [{int(v): int(rng.integers(-1, int(inst.dom[v]))) for v in rng.choice(ev_vars, size=3, replace=False)}
              for _ in range(3 + 10 * steps)]
-    st = gb.UtilState(inst, "mbe", 20, ibound_mode="sep", use_graph=True, evidence_vars=ev_vars)
-    st.bind()
-    walls = []
-    for k, ev in enumerate(draws):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st.condition(ev)
-        st.run()
-        b = st.value().bound
-        t1 = time.perf_counter()
-        if k >= 3:
-            walls.append(t1 - t0)
-    st.free()
-    fresh = []
-    for k, ev in enumerate(draws[: 3 + steps]):
-        aug = synth.with_evidence(inst, {v: a for v, a in ev.items() if a >= 0})
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st2 = gb.UtilState(aug, "mbe", 20, ibound_mode="sep", use_graph=True)
-        st2.bind()
-        st2.run()
-        b2 = st2.value().bound
-        st2.free()
-        t1 = time.perf_counter()
-        if k >= 3:
-            fresh.append(t1 - t0)
-    out["conditioned_mbe_bn200"] = {
-        "workload": "MBE i=20 bound of the n=200 Bayesian network under changing evidence "
-                    "(16 evidence variables, 3 re-clamped per bound)",
-        "bounds_per_s": 1.0 / statistics.median(walls), "ms_per_bound": 1e3 * statistics.median(walls),
-        "replan_ms_per_bound": 1e3 * statistics.median(fresh),
-        "speedup_vs_replan": statistics.median(fresh) / statistics.median(walls)}
-    del b, b2
+    for z in (20, 10):
+        st = gb.UtilState(inst, "mbe", z, ibound_mode="sep", use_graph=True, evidence_vars=ev_vars)
+        st.bind()
+        walls = []
+        for k, ev in enumerate(draws):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st.condition(ev)
+            st.run()
+            st.value()
+            t1 = time.perf_counter()
+            if k >= 3:
+                walls.append(t1 - t0)
+        st.free()
+        fresh = []
+        for k, ev in enumerate(draws[: 3 + steps]):
+            aug = synth.with_evidence(inst, {v: a for v, a in ev.items() if a >= 0})
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st2 = gb.UtilState(aug, "mbe", z, ibound_mode="sep")
+            st2.bind()
+            st2.run()
+            st2.value()
+            st2.free()
+            t1 = time.perf_counter()
+            if k >= 3:
+                fresh.append(t1 - t0)
+        out[f"conditioned_mbe_bn200_i{z}"] = {
+            "workload": f"MBE i={z} bound of the n=200 Bayesian network under changing evidence "
+                        "(16 evidence variables, 3 re-clamped per bound)",
+            "bounds_per_s": 1.0 / statistics.median(walls), "ms_per_bound": 1e3 * statistics.median(walls),
+            "replan_ms_per_bound": 1e3 * statistics.median(fresh),
+            "speedup_vs_replan": statistics.median(fresh) / statistics.median(walls)}
     # sum-product (-log Z) on the 12x12 grid shape: a pairwise MRF, d = 4
     inst = synth.grid_mrf(12, 12, 4, seed=0, unary=False)
     st = gb.UtilState(inst, "sum", order="best", use_graph=True, autotune_cache=TUNE_CACHE)
