@@ -288,7 +288,7 @@ def secondary(torch, gb, synth, steps):
                             "entries_per_s": info["util_entries"] / (m * 1e-3), "gbs": gbs,
                             "hbm_frac": gbs / peak, "block_threads": thr, "rows_per_item": rows,
                             "neg_log_z": logz}
-    out["serving"] = serve_bench(torch, gb, synth, int(os.environ.get("GPUBE_SERVE_REQUESTS", "400")))
+    out["serving"] = serve_bench(torch, gb, synth, int(os.environ.get("GPUBE_SERVE_REQUESTS", "2000")))
     return out
 
 
