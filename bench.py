@@ -424,6 +424,38 @@ def sweep_case(args):
     return 0
 
 
+def instance_case(args, which):
+    """One instance for kernel profiles, no autotuning (launch shape from
+    --threads / --rows): "wide100" = BE on a random network n=8, d=100
+    (warp-per-row path, its first level holds 98% of the work); "er_mbe" =
+    the Erdos-Renyi MBE (log2 bound 16), level-batched.  Prints the UTIL ms."""
+    import torch
+    import synth
+    import paper_1608_05288_gb300 as gb
+    from paper_1608_05288_gb300 import _build
+    _build.build()
+    kw = dict(use_graph=True)
+    if args.threads:
+        kw["block_threads"] = args.threads
+    if args.rows:
+        kw["rows_per_item"] = args.rows
+    if which == "wide100":
+        st = gb.UtilState(synth.random_network_wcsp(8, 100, 0.4, seed=1), "be", order="best", **kw)
+    else:
+        st = gb.UtilState(synth.config_instance(2, 0), "mbe", 16, ibound_mode="log2", **kw)
+    st.bind()
+    info = st.info()
+    ms = []
+    for k in range(args.warmup + args.steps):
+        st.run()
+        st.sync()
+        if k >= args.warmup:
+            ms.append(st.times()[0])
+    print(json.dumps({"case": which, "util_ms": statistics.median(ms), "util_entries": info["util_entries"],
+                      "launches": info["n_levels"], "alg_bytes": info["alg_bytes"]}), flush=True)
+    return 0
+
+
 def grid_rows_case(args, rows=3, sum_product=False):
     """BE on the first `rows` rows of the headline grid (same tables, natural
     order, every bucket of row 1 is a full 4^13-entry bucket), a few GB on
@@ -472,7 +504,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-secondary", action="store_true")
-    ap.add_argument("--case", default="", choices=["", "bucket13", "grid3", "grid12", "mrf3", "sweep"])
+    ap.add_argument("--case", default="",
+                    choices=["", "bucket13", "grid3", "grid12", "mrf3", "sweep", "wide100", "er_mbe"])
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0)
     args = ap.parse_args()
@@ -488,6 +521,8 @@ def main():
         return grid_rows_case(args, 3, sum_product=True)
     if args.case == "sweep":
         return sweep_case(args)
+    if args.case in ("wide100", "er_mbe"):
+        return instance_case(args, args.case)
 
     import torch
     import torch.distributed as dist
