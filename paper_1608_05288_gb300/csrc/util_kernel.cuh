@@ -910,10 +910,24 @@ __device__ __noinline__ void item_anyD_anyF(const TaskDev *__restrict__ tkp, con
     }
 }
 
+// Order-preserving map of a non-NaN float to uint32 (unsigned order of the
+// keys = numeric order of the floats), and its inverse.
+__device__ __forceinline__ uint32_t float_key(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_float(uint32_t k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
 // Wide domains (d >= 32): a warp computes one output row at a time, lane j
 // holding x_i's values j, j + 32, ...; every input's run is read by one
-// coalesced warp access per 32 values, each lane keeps its first minimum and
-// the warp combines (value, index) pairs by shuffles, ties to the lower index.
+// coalesced warp access per 32 values.  The row minimum is one warp min
+// (redux) over each lane's minimum (floats as order-preserving keys), its
+// first argmin a second warp min over the lowest value index that holds it.
 // The warp's row is lo (a lo chunk of a wide task has one row per warp); the
 // rows of two consecutive values of u are loaded before either is reduced,
 // so that two rows' loads are in flight.  RUNS = 32-value runs per lane
@@ -929,35 +943,42 @@ __device__ __noinline__ void item_wide(const TaskDev *__restrict__ tkp, const un
     const int F = tk.F, d = tk.d, R0 = tk.R0;
     const int32_t *du = tk.A + static_cast<int64_t>(tk.G) * tk.sa;
     T *out = static_cast<T *>(tk.out);
-    const T *p[FC > 0 ? FC : 1];
-#pragma unroll
-    for (int f = 0; f < FC; ++f) p[f] = (f < F) ? input_base<T>(tk.in[f], stage) : nullptr;
     const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * tk.sb;
+    // with the input count a template bound, each input's base (its row lo
+    // included) and u stride stay in registers for the whole item
+    const T *p[FC > 0 ? FC : 1];
+    int32_t pu[FC > 0 ? FC : 1];
+#pragma unroll
+    for (int f = 0; f < FC; ++f) {
+        p[f] = (f < F) ? input_base<T>(tk.in[f], stage) + Brow[f] : nullptr;
+        pu[f] = (f < F) ? du[1 + f] : 0;
+    }
     // minimum and first argmin of one row's sums (sum-product: -log sum exp),
-    // written by lane 0
+    // written by lane 0; every lane holds at least one value (d >= 32)
     auto finish = [&](const A (&acc)[RUNS], int o) {
-        A best = A(0);
-        int bi = -1;
+        uint32_t m = 0xffffffffu;
 #pragma unroll
         for (int j = 0; j < RUNS; ++j) {
-            const int l = lane + 32 * j;
-            if (l < d && (bi < 0 || acc[j] < best)) {
-                best = acc[j];
-                bi = l;
+            if (lane + 32 * j < d) {
+                uint32_t key;
+                if constexpr (std::is_same<A, uint32_t>::value) key = acc[j];
+                else key = float_key(acc[j]);
+                m = key < m ? key : m;
             }
         }
+        m = __reduce_min_sync(0xffffffffu, m);
+        A best;
+        if constexpr (std::is_same<A, uint32_t>::value) best = m;
+        else best = key_float(m);
+        uint32_t bi = 0;
+        if constexpr (!C::kSum) {
+            uint32_t li = 0xffffffffu;
 #pragma unroll
-        for (int s = 16; s > 0; s >>= 1) {
-            const A ob = __shfl_xor_sync(0xffffffffu, best, s);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, s);
-            if (oi >= 0 && (bi < 0 || ob < best || (!(best < ob) && oi < bi))) {
-                best = ob;
-                bi = oi;
-            }
-        }
-        if constexpr (C::kSum) {
-            // every lane now holds the row minimum: sum exp(min - s_l) over
-            // the lane's values, then over the warp
+            for (int j = RUNS - 1; j >= 0; --j)
+                if (lane + 32 * j < d && acc[j] == best) li = lane + 32 * j;
+            bi = __reduce_min_sync(0xffffffffu, li);
+        } else {
+            // sum exp(min - s_l) over the lane's values, then over the warp
             if (best < kInfF) {
                 float t = 0.f;
 #pragma unroll
@@ -981,9 +1002,16 @@ __device__ __noinline__ void item_wide(const TaskDev *__restrict__ tkp, const un
 #pragma unroll
             for (int j = 0; j < RUNS; ++j) a0[j] = a1[j] = A(0);
             for (int f = 0; f < F; ++f) {
-                const T *q0 = (FC > 0 && f < FC ? p[f] : input_base<T>(tk.in[f], stage)) +
-                              (Ar[1 + f] + u * du[1 + f] + Brow[f]);
-                const T *q1 = q0 + du[1 + f];
+                const T *q0;
+                int32_t step;
+                if (FC > 0 && f < FC) {
+                    step = pu[f];
+                    q0 = p[f] + (Ar[1 + f] + u * step);
+                } else {
+                    step = du[1 + f];
+                    q0 = input_base<T>(tk.in[f], stage) + (Ar[1 + f] + u * step + Brow[f]);
+                }
+                const T *q1 = q0 + step;
 #pragma unroll
                 for (int j = 0; j < RUNS; ++j) {
                     const int l = lane + 32 * j;

@@ -296,6 +296,30 @@ def test_wide_domains_warp_shuffle(orc, d):
                 assert fp_close(res.bound, run.bound)
 
 
+@pytest.mark.parametrize("d", [32, 100, 200])
+def test_wide_domains_ties_fp32(orc, d):
+    # fp32 costs on a few integer levels (sums exact in fp32 and fp64, many
+    # ties per row, some +inf): the warp-min path must give the oracle's
+    # minima and first argmins exactly
+    rng = np.random.default_rng(d)
+    dom = np.full(4, d, np.int32)
+    scopes = [np.array(s, np.int32) for s in ([0, 1], [1, 2], [2, 3], [0, 3], [1], [3, 1])]
+    tables = []
+    for s in scopes:
+        t = rng.integers(0, 4, size=int(np.prod(dom[s]))).astype(np.float64)
+        t[rng.random(t.size) < 0.05] = np.inf
+        tables.append(t)
+    inst = synth.Instance(f"ties{d}", dom, scopes, tables, "real", 1 << 30)
+    o, _ = orc.minfill(inst)
+    run = orc.eliminate(inst, o, "be")
+    st, res = run_state(inst, "be", order="given", order_array=o)
+    for t, T in enumerate(run.tasks):
+        cost, arg = st.fetch(t)
+        assert np.array_equal(cost.astype(np.float64), T.out), f"task {t} costs"
+        assert np.array_equal(arg, T.arg), f"task {t} argmin"
+    assert res.bound == run.bound and list(res.assignment) == list(run.sigma)
+
+
 def test_paper_random_network_d100(orc):
     # the shape of the paper's random networks with d = 100 (Section 8.1, p2 = 0.5)
     inst = synth.random_network_wcsp(6, 100, 0.3, seed=3)
