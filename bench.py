@@ -128,26 +128,28 @@ class Clocks:
                 "samples": len(sm)}
 
 
-CPU_ROWS = 4  # grid rows in the oracle's bounded sample
+CPU_ROWS = 4  # grid rows in the oracle's bounded sample (all host cores)
+CPU_ROWS_1T = 2  # grid rows in the single-thread sample
 
 
-def cpu_sample_instance():
-    """The first CPU_ROWS rows of the headline grid (same tables, same
-    natural order): a bounded piece of the same workload for the oracle."""
+def cpu_sample_instance(rows=CPU_ROWS):
+    """The first `rows` rows of the headline grid (same tables, same natural
+    order): a bounded piece of the same workload for the oracle."""
     import synth
     inst = synth.config_instance(1, 0)
-    nv = 12 * CPU_ROWS
+    nv = 12 * rows
     keep = [j for j, s in enumerate(inst.scopes) if int(np.max(s)) < nv]
-    return synth.Instance(f"grid12x12_rows0-{CPU_ROWS - 1}", inst.dom[:nv].copy(),
+    return synth.Instance(f"grid12x12_rows0-{rows - 1}", inst.dom[:nv].copy(),
                           [inst.scopes[j] for j in keep], [inst.tables[j] for j in keep], "int",
                           inst.top_k)
 
 
-def cpu_oracle_step():
-    """One oracle pass over the bounded sample; returns (entries, seconds, threads)."""
+def cpu_oracle_step(threads=0, rows=CPU_ROWS):
+    """One oracle pass over the bounded sample, on `threads` host threads
+    (0: all); returns (entries, seconds, threads)."""
     import oracle
-    inst = cpu_sample_instance()
-    th = oracle.max_threads()
+    inst = cpu_sample_instance(rows)
+    th = threads or oracle.max_threads()
     oracle.set_threads(th)
     t0 = time.perf_counter()
     run = oracle.eliminate(inst, np.arange(inst.n), "be", tables=False)
@@ -597,7 +599,7 @@ def main():
     # end to end through the C ABI from host buffers: load, plan, upload, UTIL,
     # VALUE, result copy, in every step
     arena = torch.empty(info["arena_bytes"] + 4096, dtype=torch.uint8, device=dev)
-    e2e_s = []
+    e2e_s, plan_ms = [], []
     for k in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -607,12 +609,14 @@ def main():
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_s.append(t1 - t0)
+            plan_ms.append(r.plan_ms)
         assert r.bound == res.bound
     e2e_tot = max_over_ranks(sum(e2e_s), dev)
     h2d = sum(len(t) for t in inst.tables) * 4
     e2e = {"value": whole_job_rate(info["util_entries"], world, args.steps, e2e_tot), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24 + 4 * inst.n,
-           "ms_per_step": 1e3 * e2e_tot / args.steps}
+           "ms_per_step": 1e3 * e2e_tot / args.steps,
+           "host_plan_ms": statistics.median(plan_ms)}  # ordering, buckets, levels (inside the step)
     del arena
 
     extra = {}
@@ -624,6 +628,12 @@ def main():
         cpu = {"value": e / t, "unit": UNIT, "cores": th, "kind": "oracle",
                "sample": f"oracle BE on rows 0-{CPU_ROWS - 1} of the 12x12 grid ({12 * CPU_ROWS} variables, "
                          f"natural order, {e} joint entries, {t:.1f} s)"}
+        # the sequential oracle (one host thread), the form of the paper's
+        # CPU comparison, on a smaller piece of the same grid
+        e1, t1, _ = cpu_oracle_step(threads=1, rows=CPU_ROWS_1T)
+        cpu["single_thread"] = {"value": e1 / t1, "unit": UNIT, "cores": 1,
+                                "sample": f"oracle BE on rows 0-{CPU_ROWS_1T - 1} of the 12x12 grid "
+                                          f"({12 * CPU_ROWS_1T} variables, {e1} joint entries, {t1:.1f} s)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
