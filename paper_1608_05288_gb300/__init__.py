@@ -54,29 +54,40 @@ def _ptr(a, t=C.c_int32):
     return a.ctypes.data_as(C.POINTER(t)) if a is not None else None
 
 
+class Packed:
+    """A problem as the flat arrays of ``wcsp_desc`` (CSR scopes and tables):
+    pack once, then load it any number of times without re-marshalling."""
+
+    def __init__(self, inst):
+        self.n = int(len(inst.dom))
+        self.is_int = inst.cost_type == "int"
+        self.dom = _i32(inst.dom)
+        F = self.F = len(inst.scopes)
+        self.scope_off = np.zeros(F + 1, dtype=np.int32)
+        self.tab_off = np.zeros(F + 1, dtype=np.int64)
+        np.cumsum(np.fromiter((len(s) for s in inst.scopes), dtype=np.int32, count=F), out=self.scope_off[1:])
+        np.cumsum(np.fromiter((len(t) for t in inst.tables), dtype=np.int64, count=F), out=self.tab_off[1:])
+        self.scope = _i32(np.concatenate(inst.scopes) if F and self.scope_off[-1] else np.zeros(1))
+        if self.is_int:
+            costs = np.concatenate(inst.tables) if F else np.zeros(1)
+            self.costs = np.ascontiguousarray(np.minimum(costs, 2**31 - 1), dtype=np.int32)
+        else:
+            self.costs = np.ascontiguousarray(np.concatenate(inst.tables) if F else np.zeros(1), dtype=np.float32)
+        self.top_k = int(min(inst.top_k, 2**31 - 1)) if self.is_int else 1
+
+
 class WCSP:
-    """A problem loaded into the library (``wcsp_load``)."""
+    """A problem loaded into the library (``wcsp_load``), from an instance or
+    from its ``Packed`` arrays."""
 
     def __init__(self, inst):
         L = lib()
-        self.n = int(len(inst.dom))
-        self.is_int = inst.cost_type == "int"
-        dom = _i32(inst.dom)
-        F = len(inst.scopes)
-        scope_off = np.zeros(F + 1, dtype=np.int32)
-        tab_off = np.zeros(F + 1, dtype=np.int64)
-        np.cumsum(np.fromiter((len(s) for s in inst.scopes), dtype=np.int32, count=F), out=scope_off[1:])
-        np.cumsum(np.fromiter((len(t) for t in inst.tables), dtype=np.int64, count=F), out=tab_off[1:])
-        scope = _i32(np.concatenate(inst.scopes) if F and scope_off[-1] else np.zeros(1))
-        if self.is_int:
-            costs = np.concatenate(inst.tables) if F else np.zeros(1)
-            costs = np.ascontiguousarray(np.minimum(costs, 2**31 - 1), dtype=np.int32)
-        else:
-            costs = np.ascontiguousarray(np.concatenate(inst.tables) if F else np.zeros(1), dtype=np.float32)
-        d = _abi.WcspDesc(self.n, _ptr(dom), F, _ptr(scope_off), _ptr(scope),
-                          tab_off.ctypes.data_as(_abi.i64p), costs.ctypes.data_as(C.c_void_p),
-                          INT32_SAT if self.is_int else FP32_LOG,
-                          int(min(inst.top_k, 2**31 - 1)) if self.is_int else 1)
+        pk = inst if isinstance(inst, Packed) else Packed(inst)
+        self.n = pk.n
+        self.is_int = pk.is_int
+        d = _abi.WcspDesc(pk.n, _ptr(pk.dom), pk.F, _ptr(pk.scope_off), _ptr(pk.scope),
+                          pk.tab_off.ctypes.data_as(_abi.i64p), pk.costs.ctypes.data_as(C.c_void_p),
+                          INT32_SAT if pk.is_int else FP32_LOG, pk.top_k)
         h = C.c_void_p()
         _check(L.wcsp_load(C.byref(d), C.byref(h)))
         self.h = h

@@ -147,7 +147,9 @@ std::vector<int32_t> order_minfill(const wcsp &w, int32_t *width, int32_t give_u
     return order;
 }
 
-// Induced width along an order (Definition 1).
+// Induced width along an order (Definition 1): the largest number of
+// remaining neighbours of a variable when it is eliminated, its remaining
+// neighbours connected pairwise after each elimination (adjacency bit rows).
 int32_t induced_width(const wcsp &w, const std::vector<int32_t> &order)
 {
     const int n = w.n;
@@ -155,18 +157,25 @@ int32_t induced_width(const wcsp &w, const std::vector<int32_t> &order)
     adj.init(n);
     for (int v = 0; v < n; ++v)
         for (int u : w.adj[v]) adj.set(v, u);
-    std::vector<char> gone(n, 0);
+    const int W = adj.words;
+    std::vector<uint64_t> alive(W, 0), nbm(W);
+    for (int v = 0; v < n; ++v) alive[v / 64] |= 1ULL << (v % 64);
     int32_t wmax = 0;
     std::vector<int> nb;
     for (int v : order) {
+        alive[v / 64] &= ~(1ULL << (v % 64));
+        const uint64_t *r = adj.row(v);
         nb.clear();
-        for (int u = 0; u < n; ++u)
-            if (!gone[u] && adj.test(v, u)) nb.push_back(u);
+        for (int k = 0; k < W; ++k) {
+            nbm[k] = r[k] & alive[k];
+            for (uint64_t x = nbm[k]; x; x &= x - 1) nb.push_back(k * 64 + __builtin_ctzll(x));
+        }
         wmax = std::max<int32_t>(wmax, static_cast<int32_t>(nb.size()));
-        for (int a : nb)
-            for (int b : nb)
-                if (a != b) adj.set(a, b);
-        gone[v] = 1;
+        for (int a : nb) {  // a gains every other remaining neighbour of v
+            uint64_t *ra = adj.row(a);
+            for (int k = 0; k < W; ++k) ra[k] |= nbm[k];
+            ra[a / 64] &= ~(1ULL << (a % 64));
+        }
     }
     return wmax;
 }

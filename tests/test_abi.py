@@ -237,3 +237,14 @@ def test_minfill_order_matches_oracle_larger_graphs(orc, seed):
     except gb.GpubeError:
         pytest.skip("tables too large to plan")
     assert list(st.order()) == list(o)
+
+
+def test_packed_arrays_load_the_same_problem():
+    # WCSP from the flat wcsp_desc arrays (packed once) and from the instance
+    # give the same plan, for integer and real costs
+    for inst in (synth.config_instance(0, 1), synth.bayes_net_mpe(40, 2)):
+        pk = gb.Packed(inst)
+        a = gb.UtilState(gb.WCSP(inst), "be").info()
+        for _ in range(2):  # the packed arrays are reusable
+            b = gb.UtilState(gb.WCSP(pk), "be").info()
+            assert a == b
