@@ -430,7 +430,10 @@ def instance_case(args, which):
     """One instance for kernel profiles, no autotuning (launch shape from
     --threads / --rows): "wide100" = BE on a random network n=8, d=100
     (warp-per-row path, its first level holds 98% of the work); "er_mbe" =
-    the Erdos-Renyi MBE (log2 bound 16), level-batched.  Prints the UTIL ms."""
+    the Erdos-Renyi MBE (log2 bound 16), level-batched; "mpe_tasks" = the MPE
+    bound of the n=200 Bayesian network (MBE i=20, fp32), one launch per
+    mini-bucket in task order, no graph (a launch list then times each
+    mini-bucket).  Prints the UTIL ms."""
     import torch
     import synth
     import paper_1608_05288_gb300 as gb
@@ -443,6 +446,9 @@ def instance_case(args, which):
         kw["rows_per_item"] = args.rows
     if which == "wide100":
         st = gb.UtilState(synth.random_network_wcsp(8, 100, 0.4, seed=1), "be", order="best", **kw)
+    elif which == "mpe_tasks":
+        kw.update(use_graph=False, batched=False)
+        st = gb.UtilState(synth.config_instance(3, 0), "mbe", 20, ibound_mode="sep", **kw)
     else:
         st = gb.UtilState(synth.config_instance(2, 0), "mbe", 16, ibound_mode="log2", **kw)
     st.bind()
@@ -454,7 +460,8 @@ def instance_case(args, which):
         if k >= args.warmup:
             ms.append(st.times()[0])
     print(json.dumps({"case": which, "util_ms": statistics.median(ms), "util_entries": info["util_entries"],
-                      "launches": info["n_levels"], "alg_bytes": info["alg_bytes"]}), flush=True)
+                      "launches": info["n_tasks"] if which == "mpe_tasks" else info["n_levels"],
+                      "alg_bytes": info["alg_bytes"]}), flush=True)
     return 0
 
 
@@ -507,7 +514,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--case", default="",
-                    choices=["", "bucket13", "grid3", "grid12", "mrf3", "sweep", "wide100", "er_mbe"])
+                    choices=["", "bucket13", "grid3", "grid12", "mrf3", "sweep", "wide100", "er_mbe", "mpe_tasks"])
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0)
     args = ap.parse_args()
@@ -523,7 +530,7 @@ def main():
         return grid_rows_case(args, 3, sum_product=True)
     if args.case == "sweep":
         return sweep_case(args)
-    if args.case in ("wide100", "er_mbe"):
+    if args.case in ("wide100", "er_mbe", "mpe_tasks"):
         return instance_case(args, args.case)
 
     import torch

@@ -392,8 +392,10 @@ __device__ __noinline__ void item_fixed_anyF(const TaskDev *__restrict__ tkp, co
 // independent loads of the large input are in flight per thread), and each
 // row adds its NR runs, takes the min and first argmin over x_i and writes
 // both.  Row offsets advance by the stride of u: a row costs NR vector
-// loads, the adds, the argmin and two stores.
-template <typename C, int D, int FC, int NR>
+// loads, the adds, the argmin and two stores.  U > 0: the radix R0 of u is
+// U, and the per-row runs of all U rows of the NG groups are loaded before
+// any of them is summed (U x NG x NR loads in flight per thread).
+template <typename C, int D, int FC, int NR, int U = 0>
 __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo, int g0,
                                               int g1, uint32_t k)
 {
@@ -444,9 +446,11 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
                 for (int l = 0; l < D; ++l) pre[j][l] = base[l];
             }
             // all group-input loads of the NG groups first, then the sums
+            // (inputs [nlo, ngi); the unrolled loop branches past the rest)
 #pragma unroll
-            for (int f = 0; f < FC; ++f)
-                if (f >= nlo && f < ngi) {
+            for (int f = 0; f < FC; ++f) {
+                if (f >= ngi) break;
+                if (f >= nlo) {
                     T x[NG][D];
 #pragma unroll
                     for (int j = 0; j < NG; ++j) load_run<D>(gp[f] + a[j][1 + f], x[j]);
@@ -455,6 +459,7 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
 #pragma unroll
                         for (int l = 0; l < D; ++l) pre[j][l] = C::add(pre[j][l], x[j][l], k);
                 }
+            }
 #pragma unroll
             for (int j = 0; j < NG; ++j) {
                 oo[j] = a[j][0] + lo;
@@ -468,6 +473,35 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
             }
         }
         const int nj = (g + 1 < g1) ? NG : 1;
+        if constexpr (U > 0 && NR > 0) {
+            T v[U][NG][NR][D];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int j = 0; j < NG; ++j)
+#pragma unroll
+                    for (int r = 0; r < NR; ++r)
+                        if (j < nj) load_run<D>(rp[r] + (ro[j][r] + u * dr[r]), v[u][j][r]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int j = 0; j < NG; ++j)
+                    if (j < nj) {
+                        A acc[D];
+#pragma unroll
+                        for (int l = 0; l < D; ++l) acc[l] = pre[j][l];
+#pragma unroll
+                        for (int r = 0; r < NR; ++r)
+#pragma unroll
+                            for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[u][j][r][l], k);
+                        int bi;
+                        const A best = reduce_run<C, D>(acc, bi);
+                        const int32_t o = oo[j] + u * d0;
+                        out[o] = C::store(best);
+                        if constexpr (!C::kSum) arg[o] = static_cast<uint8_t>(bi);
+                    }
+            continue;
+        }
         for (int u = 0; u < R0; ++u) {
 #pragma unroll
             for (int j = 0; j < NG; ++j) {
@@ -618,24 +652,8 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
         }
         cp_async_commit();
     };
-    // one output row: b (partial sum) + x (group run) + the NRG per-row runs
-    auto row = [&](const A (&b)[D], const T (&x)[D], int32_t (&ro)[R], int32_t o) {
-        A acc[D];
-        if constexpr (NRG == 0 && kInt) {
-#pragma unroll
-            for (int l = 0; l < D; ++l) acc[l] = b[l] + static_cast<A>(x[l]);  // <= 2k, no wrap
-        } else {
-#pragma unroll
-            for (int l = 0; l < D; ++l) acc[l] = C::add(b[l], x[l], k);
-#pragma unroll
-            for (int r = 0; r < NRG; ++r) {
-                T v[D];
-                load_run<D>(rp[r] + ro[r], v);
-                ro[r] += dr[r];
-#pragma unroll
-                for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
-            }
-        }
+    // minimum (or -log sum exp) and first argmin of one row's sums, written
+    auto reduce_store = [&](A (&acc)[D], int32_t o) {
         A best = acc[0];
         int bi = 0;
 #pragma unroll
@@ -660,6 +678,26 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
         }
         out[o] = C::store(best);
         if constexpr (!C::kSum) arg[o] = static_cast<uint8_t>(bi);
+    };
+    // one output row: b (partial sum) + x (group run) + the NRG per-row runs
+    auto row = [&](const A (&b)[D], const T (&x)[D], int32_t (&ro)[R], int32_t o) {
+        A acc[D];
+        if constexpr (NRG == 0 && kInt) {
+#pragma unroll
+            for (int l = 0; l < D; ++l) acc[l] = b[l] + static_cast<A>(x[l]);  // <= 2k, no wrap
+        } else {
+#pragma unroll
+            for (int l = 0; l < D; ++l) acc[l] = C::add(b[l], x[l], k);
+#pragma unroll
+            for (int r = 0; r < NRG; ++r) {
+                T v[D];
+                load_run<D>(rp[r] + ro[r], v);
+                ro[r] += dr[r];
+#pragma unroll
+                for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
+            }
+        }
+        reduce_store(acc, o);
     };
 #pragma unroll
     for (int s = 0; s < KP; ++s) issue(g0 + s, s);
@@ -720,6 +758,28 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
                 o += d0;
             }
             issue(g + KP, slot);  // the slot's data has been consumed
+        } else if constexpr (FOLD && U > 0 && NRG > 0) {
+            // the per-row runs of all U rows are loaded before any row is
+            // summed (stores to the output would otherwise keep later loads
+            // behind them)
+            T rv[U][R][D];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int r = 0; r < NRG; ++r) load_run<D>(rp[r] + (ro[r] + u * dr[r]), rv[u][r]);
+            issue(g + KP, slot);  // x is in registers
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                A acc[D];
+#pragma unroll
+                for (int l = 0; l < D; ++l) acc[l] = C::add(bur[u][l], x[l], k);
+#pragma unroll
+                for (int r = 0; r < NRG; ++r)
+#pragma unroll
+                    for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], rv[u][r][l], k);
+                reduce_store(acc, o);
+                o += d0;
+            }
         } else if constexpr (FOLD) {
 #pragma unroll
             for (int u = 0; u < (U ? U : UMAX); ++u)
@@ -776,7 +836,24 @@ __device__ __forceinline__ void item_fixed(const TaskDev *__restrict__ tkp, cons
                     else if (tk.R0 == 2) item_pipe<C, D, 0, true, 2>(tkp, stage, pipe, arows, lo, g0, g1, k);
                     else item_pipe<C, D, 0, true>(tkp, stage, pipe, arows, lo, g0, g1, k);
                     break;
-                case 1: item_pipe<C, D, 1, true>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                case 1:  // one per-row input: its runs for the U rows loaded together
+                         // (domains up to 4; larger ones would spill them)
+                    if constexpr (D <= 4) {
+                        if (tk.R0 == 2) {
+                            item_pipe<C, D, 1, true, 2>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                            break;
+                        }
+                        if (tk.R0 == 3) {
+                            item_pipe<C, D, 1, true, 3>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                            break;
+                        }
+                        if (tk.R0 == 4) {
+                            item_pipe<C, D, 1, true, 4>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                            break;
+                        }
+                    }
+                    item_pipe<C, D, 1, true>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    break;
                 default: item_pipe<C, D, 2, true>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
                 }
             } else {
@@ -791,7 +868,20 @@ __device__ __forceinline__ void item_fixed(const TaskDev *__restrict__ tkp, cons
     }
     switch (tk.F - tk.n_gi) {
     case 0: item_fixed_nr<C, D, FC, 0>(tkp, stage, lo, g0, g1, k); break;
-    case 1: item_fixed_nr<C, D, FC, 1>(tkp, stage, lo, g0, g1, k); break;
+    case 1:  // one per-row input: the rows of u unrolled for small radices and
+             // domains (larger ones would spill the loaded runs)
+        if constexpr (D <= 3) {
+            if (tk.R0 == 2) {
+                item_fixed_nr<C, D, FC, 1, 2>(tkp, stage, lo, g0, g1, k);
+                break;
+            }
+            if (tk.R0 == 3) {
+                item_fixed_nr<C, D, FC, 1, 3>(tkp, stage, lo, g0, g1, k);
+                break;
+            }
+        }
+        item_fixed_nr<C, D, FC, 1>(tkp, stage, lo, g0, g1, k);
+        break;
     case 2: item_fixed_nr<C, D, FC, 2>(tkp, stage, lo, g0, g1, k); break;
     default:
         if constexpr (FC <= 3) item_fixed_nr<C, D, FC, 3>(tkp, stage, lo, g0, g1, k);
