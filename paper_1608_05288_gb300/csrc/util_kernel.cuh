@@ -500,28 +500,28 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
                         out[o] = C::store(best);
                         if constexpr (!C::kSum) arg[o] = static_cast<uint8_t>(bi);
                     }
-            continue;
-        }
-        for (int u = 0; u < R0; ++u) {
+        } else {
+            for (int u = 0; u < R0; ++u) {
 #pragma unroll
-            for (int j = 0; j < NG; ++j) {
-                if (j < nj) {
-                    A acc[D];
+                for (int j = 0; j < NG; ++j) {
+                    if (j < nj) {
+                        A acc[D];
 #pragma unroll
-                    for (int l = 0; l < D; ++l) acc[l] = pre[j][l];
+                        for (int l = 0; l < D; ++l) acc[l] = pre[j][l];
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        T v[D];
-                        load_run<D>(rp[r] + ro[j][r], v);
-                        ro[j][r] += dr[r];
+                        for (int r = 0; r < NR; ++r) {
+                            T v[D];
+                            load_run<D>(rp[r] + ro[j][r], v);
+                            ro[j][r] += dr[r];
 #pragma unroll
-                        for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
+                            for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
+                        }
+                        int bi;
+                        const A best = reduce_run<C, D>(acc, bi);
+                        out[oo[j]] = C::store(best);
+                        if constexpr (!C::kSum) arg[oo[j]] = static_cast<uint8_t>(bi);
+                        oo[j] += d0;
                     }
-                    int bi;
-                    const A best = reduce_run<C, D>(acc, bi);
-                    out[oo[j]] = C::store(best);
-                    if constexpr (!C::kSum) arg[oo[j]] = static_cast<uint8_t>(bi);
-                    oo[j] += d0;
                 }
             }
         }
