@@ -560,7 +560,10 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     constexpr int R = NRG > 0 ? NRG : 1;
     constexpr int CH = (D % 4 == 0) ? 16 : (D % 2 == 0) ? 8 : 4;  // bytes per copy
     constexpr int NCH = D * 4 / CH;                                  // copies per run
-    constexpr int KP = D <= 4 ? kPipeSmall : kPipe;                  // groups in flight (pipe_depth(D))
+    // groups in flight (pipe_depth(D)); packed-key rows hold the per-u
+    // partial sums in registers once the prologue has read them back, and
+    // their four shared-memory slots become four more pipeline slots
+    constexpr int KP = (D <= 4 ? kPipeSmall : kPipe) + (PK ? 4 : 0);
     const int NT = blockDim.x, tid = threadIdx.x;
     const int nlo = tk.n_lo, ngi = tk.n_gi, R0 = tk.R0;
     const int rg0 = FOLD ? tk.n_uo : ngi;  // first general per-row input
@@ -579,7 +582,9 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     // the slots' A rows, and the per-u partial sums, each laid out
     // [index][chunk][thread] so that the 16-byte reads are conflict-free
     const uint32_t pipe_s = smem_addr(pipe);
-    const uint32_t bus_s = pipe_s + static_cast<uint32_t>(KP * NCH * NT * CH);
+    // (PK: the partial sums occupy the last four pipeline slots until they
+    // are read back into registers)
+    const uint32_t bus_s = pipe_s + static_cast<uint32_t>((PK ? KP - 4 : KP) * NCH * NT * CH);
     const uint32_t arows_s = smem_addr(arows);
     A bur[U ? U : 1][D];
     // SF: sum-product rows of two terms with the radix of u fixed.  Because
@@ -591,6 +596,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     // apart; or +inf terms) the row is recomputed from the raw terms.
     constexpr bool SF = C::kSum && FOLD && NRG == 0 && U > 0;
     float mbu[SF ? U : 1];
+    int32_t zdep = 0;
     if constexpr (FOLD) {
         for (int u = 0; u < R0; ++u) {
             A bu[D];
@@ -613,6 +619,15 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
             for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int l = 0; l < D; ++l) bur[u][l] = (bur[u][l] << 2) | static_cast<uint32_t>(l);
+            // a zero that depends on every value read back: the copies into
+            // the slots that held the partial sums take it in their address,
+            // so they are issued only after those shared loads returned
+            uint32_t all = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int l = 0; l < D; ++l) all |= bur[u][l];
+            asm volatile("and.b32 %0, %1, 0;" : "=r"(zdep) : "r"(all));
         }
         if constexpr (SF) {
             // partial sums as (minimum, exp(minimum - b_l)); the raw values stay
@@ -642,9 +657,9 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     uint8_t *arg = tk.arg;
     // the item's A rows are in shared memory (arows[(g - g0) * SA + slot]);
     // each pipeline slot holds, per thread, one group run
-    auto issue = [&](int g, int slot) {
+    auto issue = [&](int g, int slot, int32_t zoff = 0) {
         if (g < g1) {
-            const T *src = gp + lds_int(arows_s + static_cast<uint32_t>(((g - g0) * SA + 1 + gf) * 4));
+            const T *src = gp + (lds_int(arows_s + static_cast<uint32_t>(((g - g0) * SA + 1 + gf) * 4)) + zoff);
 #pragma unroll
             for (int c = 0; c < NCH; ++c)
                 cp_async_s<CH>(pipe_s + static_cast<uint32_t>(((slot * NCH + c) * NT + tid) * CH),
@@ -700,7 +715,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
         reduce_store(acc, o);
     };
 #pragma unroll
-    for (int s = 0; s < KP; ++s) issue(g0 + s, s);
+    for (int s = 0; s < KP; ++s) issue(g0 + s, s, (PK && s >= KP - 4) ? zdep : 0);
     int slot = 0;
     for (int g = g0; g < g1; ++g) {
         cp_async_wait<KP - 1>();
