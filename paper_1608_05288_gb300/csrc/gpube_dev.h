@@ -85,7 +85,9 @@ constexpr int kPipe = 4;
 constexpr int kPipeSmall = 8;  // the depth for runs of at most 16 bytes (d <= 4)
 constexpr int kMaxPipeRows = 256;
 // Pipeline depth and shared-memory bytes per thread of the cp.async path for
-// domain d: the slots plus four per-u partial sums, 4d bytes each.
+// domain d: the slots plus four per-u partial sums, 4d bytes each (the
+// packed-key rows read their partial sums back into registers and then use
+// those four as pipeline slots too).
 constexpr int pipe_depth(int d) { return d <= 4 ? kPipeSmall : kPipe; }
 constexpr int pipe_bytes_per_thread(int d) { return (pipe_depth(d) + 4) * 4 * d; }
 
