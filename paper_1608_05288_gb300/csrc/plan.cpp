@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <chrono>
+#include <cstdint>
 #include <numeric>
 
 #include "gpube_internal.h"
@@ -378,6 +379,10 @@ int build_plan(const wcsp &w, int kind, int i_bound, const int32_t *parent, cons
     // 3. Algorithm 1 / 2: buckets, partitions, bucket functions
     const bool mbe = kind_mbe(kind);
     std::vector<char> in_union(n, 0);  // BE: variables of the bucket's single mini-bucket
+    // scratch reused across buckets: mini-bucket variable sets and function
+    // lists (the first nmb entries are live), a separator, a scope union
+    std::vector<std::vector<int32_t>> mb_funcs, mb_vars;
+    std::vector<int32_t> sep, fv, uni;
     for (int t = 0; t < n; ++t) {
         const int v = P.order[t];
         std::vector<int32_t> &B = bucket[v];
@@ -387,50 +392,59 @@ int build_plan(const wcsp &w, int kind, int i_bound, const int32_t *parent, cons
             if (kind_sum(kind)) P.const_sum += -std::log(static_cast<double>(w.dom[v]));
             continue;
         }
-        std::stable_sort(B.begin(), B.end(), [&](int a, int b) {
+        // arity descending, then creation order (a total order: the sort is stable)
+        std::sort(B.begin(), B.end(), [&](int a, int b) {
             if (P.funcs[a].scope.size() != P.funcs[b].scope.size())
                 return P.funcs[a].scope.size() > P.funcs[b].scope.size();
             return a < b;
         });
-        std::vector<std::vector<int32_t>> mb_funcs, mb_vars;  // vars kept sorted by id
+        size_t nmb = 0;  // mini-buckets of this bucket; their variables kept sorted by id
+        auto open_mb = [&]() {
+            if (mb_vars.size() <= nmb) {
+                mb_vars.emplace_back();
+                mb_funcs.emplace_back();
+            }
+            mb_vars[nmb].clear();
+            mb_funcs[nmb].clear();
+            return nmb++;
+        };
         if (!mbe) {
             // one bucket: the union of the scopes by marks, no partition
-            mb_vars.emplace_back();
-            mb_funcs.push_back(B);
+            const size_t b0 = open_mb();
+            mb_funcs[b0] = B;
             for (int fid : B)
                 for (int u : P.funcs[fid].scope)
                     if (!in_union[u]) {
                         in_union[u] = 1;
-                        mb_vars[0].push_back(u);
+                        mb_vars[b0].push_back(u);
                     }
-            for (int u : mb_vars[0]) in_union[u] = 0;
-            std::sort(mb_vars[0].begin(), mb_vars[0].end());
+            for (int u : mb_vars[b0]) in_union[u] = 0;
+            std::sort(mb_vars[b0].begin(), mb_vars[b0].end());
         }
         for (size_t k = 0; mbe && k < B.size(); ++k) {  // Algorithm 2: first fit under the bound
             const int fid = B[k];
-            std::vector<int32_t> fv = P.funcs[fid].scope;
+            fv.assign(P.funcs[fid].scope.begin(), P.funcs[fid].scope.end());
             std::sort(fv.begin(), fv.end());
-            int placed = -1;
-            for (size_t b = 0; b < mb_vars.size() && placed < 0; ++b) {
-                std::vector<int32_t> u;
-                std::set_union(mb_vars[b].begin(), mb_vars[b].end(), fv.begin(), fv.end(), std::back_inserter(u));
-                if (mb_fits(w, o.ibound_mode, i_bound, u)) {
-                    mb_vars[b] = u;
-                    placed = static_cast<int>(b);
+            size_t placed = SIZE_MAX;
+            for (size_t b = 0; b < nmb && placed == SIZE_MAX; ++b) {
+                uni.clear();
+                std::set_union(mb_vars[b].begin(), mb_vars[b].end(), fv.begin(), fv.end(), std::back_inserter(uni));
+                if (mb_fits(w, o.ibound_mode, i_bound, uni)) {
+                    mb_vars[b].swap(uni);
+                    placed = b;
                 }
             }
-            if (placed < 0) {
-                mb_vars.push_back(fv);
-                mb_funcs.emplace_back();
-                placed = static_cast<int>(mb_vars.size()) - 1;
+            if (placed == SIZE_MAX) {
+                placed = open_mb();
+                mb_vars[placed] = fv;
             }
             mb_funcs[placed].push_back(fid);
         }
-        for (size_t b = 0; b < mb_vars.size(); ++b) {
+        for (size_t b = 0; b < nmb; ++b) {
             Task T;
             T.var = v;
             T.d = w.dom[v];
-            std::vector<int32_t> sep;
+            sep.clear();
             for (int u : mb_vars[b])
                 if (u != v) sep.push_back(u);
             T.sep = canonical(sep);
@@ -504,6 +518,9 @@ void task_strides(const wcsp &w, const Plan &P, const Task &T, std::vector<int32
 // they are read, and choose the staged inputs.
 void shape_tasks(const wcsp &w, Plan &P)
 {
+    // scratch lists reused across tasks (cleared per task)
+    std::vector<int32_t> absent, present, lo_only, group, u_only, row;
+    std::vector<int> idx;
     for (Task &T : P.tasks) {
         const int m = static_cast<int>(T.sep.size());
         const int F = static_cast<int>(T.inputs.size());
@@ -520,7 +537,8 @@ void shape_tasks(const wcsp &w, Plan &P)
         for (int f = 1; f < F; ++f)
             if (P.funcs[T.inputs[f]].size > P.funcs[T.inputs[big]].size) big = f;
         const auto &bs = P.funcs[T.inputs[big]].scope;
-        std::vector<int32_t> absent, present;
+        absent.clear();
+        present.clear();
         for (int j = m - T.L - 1; j >= 0; --j) {
             bool in = std::find(bs.begin(), bs.end(), T.sep[j]) != bs.end();
             (in ? present : absent).push_back(j);
@@ -531,7 +549,10 @@ void shape_tasks(const wcsp &w, Plan &P)
         T.G = T.H / T.R0;
         // inputs: lo digits only | hi digits but not u | u as the only hi digit | u and others
         {
-            std::vector<int32_t> lo_only, group, u_only, row;
+            lo_only.clear();
+            group.clear();
+            u_only.clear();
+            row.clear();
             for (int fid : T.inputs) {
                 const auto &fs = P.funcs[fid].scope;
                 auto has = [&](int j) { return std::find(fs.begin(), fs.end(), T.sep[j]) != fs.end(); };
@@ -555,7 +576,7 @@ void shape_tasks(const wcsp &w, Plan &P)
         // stage the smallest inputs while they fit
         T.stage_off.assign(F, -1);
         T.stage_bytes = 0;
-        std::vector<int> idx(F);
+        idx.resize(F);
         std::iota(idx.begin(), idx.end(), 0);
         std::stable_sort(idx.begin(), idx.end(),
                          [&](int a, int b) { return P.funcs[T.inputs[a]].size < P.funcs[T.inputs[b]].size; });
