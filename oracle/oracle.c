@@ -512,8 +512,10 @@ orc_run *orc_eliminate_sr(const orc_problem *P, const int *order, int mode, int 
         ++nfs;
     }
 
-    /* bucket membership kept for the value phase */
+    /* bucket membership kept for the value phase: vb[v] lists the bucket's
+     * functions, vbm[v] the mini-bucket each of them went to */
     int **vb = (int **)calloc(n + 1, sizeof(int *));
+    int **vbm = (int **)calloc(n + 1, sizeof(int *));
     int *nvb = (int *)calloc(n + 1, sizeof(int));
     unsigned char *in_u = (unsigned char *)calloc(n + 1, 1);
     unsigned char *tmp_u = (unsigned char *)calloc(n + 1, 1);
@@ -534,6 +536,7 @@ orc_run *orc_eliminate_sr(const orc_problem *P, const int *order, int mode, int 
                 }
         }
         vb[v] = (int *)malloc(sizeof(int) * (nb > 0 ? nb : 1));
+        vbm[v] = (int *)calloc(nb > 0 ? nb : 1, sizeof(int));
         nvb[v] = nb;
         memcpy(vb[v], members, sizeof(int) * nb);
         for (int k = 0; k < nb; ++k) alive[members[k]] = 0;
@@ -582,6 +585,9 @@ orc_run *orc_eliminate_sr(const orc_problem *P, const int *order, int mode, int 
             mb_of[k] = placed;
         }
         free(ar);
+        for (int k = 0; k < nb; ++k)
+            for (int q = 0; q < nb; ++q)
+                if (vb[v][q] == members[k]) vbm[v][q] = mb_of[k];
 
         for (int b = 0; b < nmb; ++b) {
             unsigned char *u = mb_u + (size_t)b * (n + 1);
@@ -683,8 +689,12 @@ orc_run *orc_eliminate_sr(const orc_problem *P, const int *order, int mode, int 
         free(fs[i].vars);
         free(fs[i].stride);
     }
-    for (int v = 0; v < n; ++v) free(vb[v]);
+    for (int v = 0; v < n; ++v) {
+        free(vb[v]);
+        free(vbm[v]);
+    }
     free(vb);
+    free(vbm);
     free(nvb);
     free(fs);
     free(alive);

@@ -86,6 +86,23 @@ def test_paper_example_plan(orc):
     assert _lib_structure(mbe) == _orc_structure(orc.eliminate(inst, np.array(order), "sep", 1))
 
 
+def test_mbe_partition_golden_plan():
+    # the library's mini-bucket partition against the hand-derived partitions
+    # of mixed-arity buckets (first fit by arity, unions on the bound accepted)
+    import json
+    with open(os.path.join(ROOT, "tests", "golden", "mbe_partition.json")) as f:
+        cases = json.load(f)["cases"]
+    for case in cases:
+        dom = np.array(case["dom"], dtype=np.int32)
+        scopes = [np.array(x, dtype=np.int32) for x in case["scopes"]]
+        tables = [np.zeros(int(np.prod([dom[v] for v in x])), dtype=np.int64) for x in scopes]
+        inst = synth.Instance(case["name"], dom, scopes, tables, "int", 1 << 30)
+        st = gb.UtilState(inst, "mbe", case["z"], order="given", order_array=case["order"],
+                          ibound_mode=case["mode"])
+        got = [{"sep": t["sep"], "inputs": t["inputs"]} for t in _lib_structure(st) if t["var"] == 0]
+        assert got == case["tasks_of_var0"], case["name"]
+
+
 @pytest.mark.parametrize("seed", range(10))
 def test_minfill_order_matches_oracle(orc, seed):
     inst = synth.random_small(seed, n=12, dmax=3, n_funcs=16, max_arity=3)

@@ -7,7 +7,7 @@ import pytest
 
 import synth
 import paper_1608_05288_gb300 as gb
-from gpu_util import fp_close, run_state, structure, orc_structure
+from gpu_util import argmin_attains_minimum, fp_close, run_state, structure, orc_structure
 
 pytestmark = pytest.mark.gpu
 
@@ -64,8 +64,13 @@ def test_random_configuration(orc, seed):
             assert np.array_equal(arg, T.arg), f"task {t}"
         else:
             assert fp_close(cost, T.out), f"task {t}"
+            if semiring == "min":  # fp32 min-sum: the argmin attains the minimum
+                assert argmin_attains_minimum(inst, run, t, arg), f"task {t} argmin"
     if exact:
         assert res.bound == run.bound and res.cost == run.cost
         assert list(res.assignment) == list(run.sigma)
     else:
         assert fp_close([res.bound], [run.bound])
+        if semiring == "min":  # the GPU's assignment re-evaluated in fp64
+            assert fp_close([orc.evaluate(inst, res.assignment)], [res.cost])
+            assert res.cost >= run.bound - 1e-4 * (1 + abs(run.bound))

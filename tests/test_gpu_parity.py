@@ -11,7 +11,7 @@ import pytest
 
 import synth
 import paper_1608_05288_gb300 as gb
-from gpu_util import check_tables, fp_close, run_state
+from gpu_util import bucket_sums_at, check_tables, fp_close, run_state
 
 pytestmark = pytest.mark.gpu
 
@@ -44,6 +44,27 @@ def test_paper_example(orc):
         check_tables(inst, st, run)
         assert res.bound == run.bound and res.cost == run.cost
         assert list(res.assignment) == list(run.sigma)
+
+
+def test_mbe_value_golden():
+    # the hand-worked MBE example: every mini-bucket's functions enter the
+    # value step of their bucket (the first or last alone picks another value)
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "mbe_value_example.json")) as f:
+        g = json.load(f)
+    dom = np.array(g["dom"], dtype=np.int32)
+    inst = synth.Instance("mbe_value", dom, [np.array(x, dtype=np.int32) for x in g["scopes"]],
+                          [np.array(t, dtype=np.int64) for t in g["tables"]], "int", 1 << 30)
+    for shape in LAUNCH_SHAPES[:3]:
+        st, res = run_state(inst, "mbe", g["z"], order="given", order_array=g["order"], ibound_mode=g["mode"],
+                            **shape)
+        for t, T in enumerate(g["tasks"]):
+            cost, arg = st.fetch(t)
+            assert [int(x) for x in cost] == T["out"] and [int(x) for x in arg] == T["arg"], t
+        assert res.bound == g["bound"] and res.cost == g["cost"]
+        assert list(res.assignment) == g["sigma"]
+        st.free()
 
 
 @pytest.mark.parametrize("shape", range(len(LAUNCH_SHAPES)))
@@ -278,6 +299,13 @@ def test_util_bucket_entry(orc, seed):
         assert np.array_equal(arg.cpu().numpy(), warg)
     else:
         assert fp_close(out.cpu().numpy(), want)
+        # the chosen value attains the minimum: the bucket sum at it, in fp64
+        dom = sep_dom + [d]
+        a = arg.cpu().numpy()
+        assert np.all(a < d)
+        s = bucket_sums_at(dom, m, list(range(m)), np.arange(rows), a,
+                           [(p + [m], t) for p, t in zip(positions, tables)])
+        assert fp_close(s, want)
 
 
 @pytest.mark.parametrize("d", [32, 40, 100, 255])

@@ -94,6 +94,43 @@ def test_paper_example_structure(orc):
     assert be.cost == be.bound
 
 
+
+# ---------------------------------- mini-bucket partition and value (Sec. 2.2)
+def _golden_instance(case, name):
+    dom = np.array(case["dom"], dtype=np.int32)
+    scopes = [np.array(s, dtype=np.int32) for s in case["scopes"]]
+    if "tables" in case:
+        tables = [np.array(t, dtype=np.int64) for t in case["tables"]]
+    else:  # the partition depends on the scopes only
+        tables = [np.zeros(int(np.prod([dom[v] for v in s])), dtype=np.int64) for s in scopes]
+    return synth.Instance(name, dom, scopes, tables, "int", 1 << 30)
+
+
+def test_mbe_partition_golden(orc):
+    # hand-derived first-fit partitions of mixed-arity buckets (R13), with
+    # unions exactly on the joint and log2 bounds
+    for case in _gold("mbe_partition.json")["cases"]:
+        inst = _golden_instance(case, case["name"])
+        run = orc.eliminate(inst, np.array(case["order"], dtype=np.int32), case["mode"], case["z"])
+        got = [{"sep": [int(x) for x in t.sep], "inputs": sorted(int(x) for x in t.inputs)}
+               for t in run.tasks if int(t.var) == 0]
+        assert got == case["tasks_of_var0"], case["name"]
+
+
+def test_mbe_value_sums_every_minibucket(orc):
+    # R11: the value of x_i minimises the sum of every function of its bucket
+    g = _gold("mbe_value_example.json")
+    inst = _golden_instance(g, "mbe_value")
+    order = np.array(g["order"], dtype=np.int32)
+    run = orc.eliminate(inst, order, g["mode"], g["z"])
+    got = [{"var": int(t.var), "sep": [int(x) for x in t.sep], "inputs": [int(x) for x in t.inputs],
+            "out": [int(x) for x in t.out], "arg": [int(x) for x in t.arg]} for t in run.tasks]
+    assert got == g["tasks"]
+    assert run.bound == g["bound"]
+    assert [int(x) for x in run.sigma] == g["sigma"]
+    assert run.cost == g["cost"]
+    assert orc.bruteforce(inst)[0] == g["optimum"]
+
 # ------------------------------------------------------ BE = exhaustive optimum
 @pytest.mark.parametrize("cost_type", ["int", "real"])
 @pytest.mark.parametrize("seed", range(12))

@@ -13,6 +13,34 @@ import test_oracle as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 
+# first fit (the oracle) and a best fit: the fitting mini-bucket whose union
+# grows least, ties to the first
+BEST_FIT_OLD = """            for (int b = 0; b < nmb && placed < 0; ++b) {
+                unsigned char *u = mb_u + (size_t)b * (n + 1);
+                memcpy(tmp_u, u, n + 1);
+                for (int j = 0; j < f->nv; ++j) tmp_u[f->vars[j]] = 1;
+                if (fits(P, mode, z, tmp_u)) {
+                    memcpy(u, tmp_u, n + 1);
+                    placed = b;
+                }
+            }"""
+BEST_FIT_NEW = """            int bgrow = 1 << 30;
+            for (int b = 0; b < nmb; ++b) {
+                unsigned char *u = mb_u + (size_t)b * (n + 1);
+                memcpy(tmp_u, u, n + 1);
+                int grow = 0;
+                for (int j = 0; j < f->nv; ++j) {
+                    grow += !tmp_u[f->vars[j]];
+                    tmp_u[f->vars[j]] = 1;
+                }
+                if (fits(P, mode, z, tmp_u) && grow < bgrow) {
+                    bgrow = grow;
+                    placed = b;
+                }
+            }
+            if (placed >= 0)
+                for (int j = 0; j < f->nv; ++j) mb_u[(size_t)placed * (n + 1) + f->vars[j]] = 1;"""
+
 # (name, text in oracle.c, replacement)
 MUTANTS = [
     ("drop a term of the bucket sum", "for (int k = 0; k < nm; ++k) s += func_eval(&fs[mbf[k]], asg);",
@@ -39,6 +67,19 @@ MUTANTS = [
     ("log-sum-exp without the shift", "acc += exp(best - sv[l]);", "acc += exp(-sv[l]);"),
     ("free variables not counted", "bound += -log((double)P->dom[v]);", "(void)0;"),
     ("partition function without the shift", "z += exp(c0 - c);", "z += exp(-c);"),
+    ("mini-buckets filled by arity ascending", "if (g_ar[x] != g_ar[y]) return g_ar[y] - g_ar[x];",
+     "if (g_ar[x] != g_ar[y]) return g_ar[x] - g_ar[y];"),
+    ("equal arities by creation id descending", "return g_id[x] - g_id[y];", "return g_id[y] - g_id[x];"),
+    ("best fit instead of first fit", BEST_FIT_OLD, BEST_FIT_NEW),
+    ("joint bound strict", "if (mode == ORC_MBE_JOINT) return k <= z;", "if (mode == ORC_MBE_JOINT) return k < z;"),
+    ("log2 bound strict", "return entries <= ldexp(1.0, z);", "return entries < ldexp(1.0, z);"),
+    ("value phase sums the first mini-bucket only",
+     "for (int k = 0; k < nvb[v]; ++k) s += func_eval(&fs[vb[v][k]], asg);",
+     "for (int k = 0; k < nvb[v]; ++k) if (vbm[v][k] == 0) s += func_eval(&fs[vb[v][k]], asg);"),
+    ("value phase sums the last mini-bucket only",
+     "for (int k = 0; k < nvb[v]; ++k) s += func_eval(&fs[vb[v][k]], asg);",
+     "for (int k = 0; k < nvb[v]; ++k) { int last = 0; for (int q = 0; q < nvb[v]; ++q) last = vbm[v][q] > last ? "
+     "vbm[v][q] : last; if (vbm[v][k] == last) s += func_eval(&fs[vb[v][k]], asg); }"),
 ]
 
 
@@ -63,6 +104,8 @@ def _pin_calls():
     for seed in range(2):
         calls.append((f"mbe_bounds_{seed}", lambda o, s=seed: pins.test_mbe_bounds_and_exactness(o, s)))
     calls.append(("dpop_sep", lambda o: pins.test_dpop_separators(o, 0)))
+    calls.append(("mbe_partition", lambda o: pins.test_mbe_partition_golden(o)))
+    calls.append(("mbe_value", lambda o: pins.test_mbe_value_sums_every_minibucket(o)))
     calls += [
         ("logz_direct", lambda o: pins.test_logz_bruteforce_is_the_partition_function(o, 1)),
         ("sum_bruteforce", lambda o: pins.test_sum_elimination_equals_bruteforce(o, 0)),
