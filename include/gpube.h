@@ -314,24 +314,39 @@ int util_bucket(int32_t cost_type, int32_t top_k, int32_t m, const int32_t *sep_
                 int32_t n_in, const void *const *in_tables, const int32_t *in_pos_off,
                 const int32_t *in_pos, void *out, uint8_t *arg, void *stream);
 
-/* The same single-bucket computation for callers that must not allocate
- * device memory: code running while a CUDA graph is being captured, loops
- * that forbid allocation after start-up, processes whose device memory is
- * owned by another allocator.  The paper has no counterpart; it is a service
- * of this library.  Its scratch (offset tables, descriptors, work counter) is
- * a fixed 4 MiB array inside the library, present on every device the
- * library is used on from load until process exit; nothing is allocated and
- * nothing is freed.  Arguments as util_bucket.  Buckets whose scratch would
- * exceed the array fail with GPUBE_ENOMEM before any GPU work (util_bucket
- * takes them).  The first call on a device, with that device current, looks
- * up the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the array and it keeps the last
- * call's contents (each call clears its counter and status first): calls
- * that may overlap on the GPU (different streams, or threads) race and must
- * be serialised by the caller.  Asynchronous on stream. */
+/* The same single-bucket computation for callers that cannot allocate
+ * device memory: loops that forbid allocation once they run (an allocation
+ * may block or fail at a moment nobody chose), and processes whose device
+ * memory is entirely owned by another allocator (a framework's caching
+ * allocator, a pre-reserved pool), where a cudaMalloc from this library
+ * would compete for memory that allocator does not know about.  The paper
+ * has no counterpart; it is a service of this library.  Its scratch (offset
+ * tables, descriptors, work counter) is a fixed 4 MiB array inside the
+ * library, present on every device the library is used on from load until
+ * process exit; nothing is allocated and nothing is freed.  Arguments as
+ * util_bucket.  A bucket whose scratch would exceed the array fails with
+ * GPUBE_ENOMEM before any CUDA call (util_bucket takes it;
+ * util_bucket_scratch_bytes tells beforehand).  The first call on a device,
+ * with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it for the process: after cudaDeviceReset
+ * that address is stale and the entry point must not be called again.  All
+ * calls share the array and it keeps the last call's contents (each call
+ * clears its counter and status first): calls that may overlap on the GPU
+ * (different streams, or threads) race and must be serialised by the
+ * caller.  Asynchronous on stream. */
 int util_bucket_noalloc(int32_t cost_type, int32_t top_k, int32_t m, const int32_t *sep_dom, int32_t d,
                         int32_t n_in, const void *const *in_tables, const int32_t *in_pos_off,
                         const int32_t *in_pos, void *out, uint8_t *arg, void *stream);
+
+/* Scratch bytes util_bucket and util_bucket_noalloc need for a bucket of
+ * this shape (arguments as util_bucket, without tables), into *bytes, and
+ * the size of util_bucket_noalloc's fixed array into *noalloc_limit (may be
+ * NULL).  Host only: no CUDA call, no GPU needed.  EINVAL on a malformed
+ * shape, ENOMEM when the output would exceed 2^31 entries.  The paper has
+ * no counterpart. */
+int util_bucket_scratch_bytes(int32_t m, const int32_t *sep_dom, int32_t d, int32_t n_in,
+                              const int32_t *in_pos_off, const int32_t *in_pos, size_t *bytes,
+                              size_t *noalloc_limit);
 
 /* Diagnostic: launch one CTA that waits, with the same time-bounded wait the
  * UTIL kernel uses on its TMA barriers, on a barrier that nothing completes.

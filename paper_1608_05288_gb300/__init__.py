@@ -359,11 +359,12 @@ def util_bucket(sep_dom, d, tables, positions, out, arg, cost_type="int", top_k=
 def util_bucket_noalloc(sep_dom, d, tables, positions, out, arg, cost_type="int", top_k=(1 << 30),
                         stream=None):
     """util_bucket for callers that cannot allocate device memory: the scratch
-    is a fixed array inside the library (``util_bucket_noalloc``).  The first
-    call on a device should come before any stream capture; calls that may
-    overlap on the GPU must be serialised by the caller."""
+    is a fixed array inside the library (``util_bucket_noalloc``).  tables,
+    out and arg are torch CUDA tensors.  The first call on a device looks up
+    the array's device address; calls that may overlap on the GPU must be
+    serialised by the caller."""
     sd = _i32(sep_dom if len(sep_dom) else [1])
-    ptrs = (C.c_void_p * len(tables))(*[t.data_ptr() if hasattr(t, "data_ptr") else int(t) for t in tables])
+    ptrs = (C.c_void_p * len(tables))(*[t.data_ptr() for t in tables])
     off = np.zeros(len(positions) + 1, dtype=np.int32)
     for i, p in enumerate(positions):
         off[i + 1] = off[i] + len(p)
@@ -371,9 +372,22 @@ def util_bucket_noalloc(sep_dom, d, tables, positions, out, arg, cost_type="int"
     st = (current_stream() if stream is None else stream)
     _check(lib().util_bucket_noalloc(INT32_SAT if cost_type == "int" else FP32_LOG, int(top_k), len(sep_dom),
                                      _ptr(sd), int(d), len(tables), ptrs, _ptr(off), _ptr(pos),
-                                     C.c_void_p(out.data_ptr() if hasattr(out, "data_ptr") else int(out)),
-                                     C.c_void_p(arg.data_ptr() if hasattr(arg, "data_ptr") else int(arg)),
-                                     C.c_void_p(st)))
+                                     C.c_void_p(out.data_ptr()), C.c_void_p(arg.data_ptr()), C.c_void_p(st)))
+
+
+def util_bucket_scratch_bytes(sep_dom, d, positions):
+    """Scratch bytes the single-bucket calls need for this bucket shape, and
+    the size of util_bucket_noalloc's fixed scratch (``util_bucket_scratch_bytes``,
+    host only: no GPU needed, nothing launched)."""
+    sd = _i32(sep_dom if len(sep_dom) else [1])
+    off = np.zeros(len(positions) + 1, dtype=np.int32)
+    for i, p in enumerate(positions):
+        off[i + 1] = off[i] + len(p)
+    pos = _i32([x for p in positions for x in p] or [0])
+    need, limit = C.c_size_t(), C.c_size_t()
+    _check(lib().util_bucket_scratch_bytes(len(sep_dom), _ptr(sd), int(d), len(positions), _ptr(off), _ptr(pos),
+                                           C.byref(need), C.byref(limit)))
+    return int(need.value), int(limit.value)
 
 
 class Server:

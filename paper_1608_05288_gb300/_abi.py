@@ -87,6 +87,8 @@ SIGNATURES = {
     "util_bucket_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, i32p, C.c_int32, C.c_int32,
                                       C.POINTER(C.c_void_p), i32p, i32p, C.c_void_p, C.c_void_p,
                                       C.c_void_p]),
+    "util_bucket_scratch_bytes": (C.c_int, [C.c_int32, i32p, C.c_int32, C.c_int32, i32p, i32p,
+                                            C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "util_selftest_wait": (C.c_int, [C.c_uint64, C.c_void_p]),
     "srv_create": (C.c_int, [C.c_size_t, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
                              C.POINTER(C.c_void_p)]),

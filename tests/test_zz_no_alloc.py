@@ -1,7 +1,7 @@
 """util_bucket_noalloc: the single-bucket UTIL kernel for callers that cannot
-allocate device memory (during a CUDA graph capture, after an allocation-free
-start-up, or when another allocator owns the device memory).  Its scratch is
-a fixed array inside the library.  The GPU test compares it with util_bucket
+allocate device memory (loops that forbid allocation once running, or
+processes whose device memory another allocator owns).  Its scratch is a
+fixed array inside the library.  The GPU test compares it with util_bucket
 on the same inputs, on two calls in a row (the second call reuses the
 scratch the first one left behind); this file is collected last."""
 import numpy as np
@@ -58,13 +58,21 @@ def test_noalloc_matches_util_bucket():
                 assert torch.equal(arg, ref_arg)
 
 
-def test_noalloc_rejects_oversized_bucket():
-    # 2^29 rows of binary variables with seven inputs: its offset tables exceed
-    # the fixed scratch, which is reported before any GPU work
+def test_scratch_query_flags_oversized_bucket():
+    from paper_1608_05288_gb300 import _build
+    _build.build()
+    # host only: the size query launches nothing and needs no GPU.  2^29 rows
+    # of binary variables with seven inputs need offset tables larger than the
+    # fixed scratch; util_bucket_noalloc makes the same check, before any CUDA
+    # call, and returns ENOMEM for such a bucket
     m = 29
     positions = [list(range(m))] + [[j] for j in range(6)]
+    need, limit = gb.util_bucket_scratch_bytes([2] * m, 2, positions)
+    assert limit == 4 << 20 and need > limit
+    # the test cases above fit
+    for sep_dom, d, pos, _ in CASES:
+        need, limit = gb.util_bucket_scratch_bytes(sep_dom, d, pos)
+        assert 0 < need <= limit
     with pytest.raises(gb.GpubeError) as e:
-        gb.util_bucket_noalloc([2] * m, 2, [256 * (i + 1) for i in range(7)], positions, 4096, 8192, "int",
-                               stream=0)
-    assert e.value.code == gb.ENOMEM
-    assert "scratch" in str(e.value)
+        gb.util_bucket_scratch_bytes([2, 3], 2, [[1, 0]])  # positions must ascend
+    assert e.value.code == gb.EINVAL
