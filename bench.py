@@ -185,13 +185,24 @@ def secondary(torch, gb, synth, steps):
     """Batched vs per-bucket MBE (Erdos-Renyi), MPE entries/s, sum-product
     -log Z on the grid shape, DCOP serving."""
     out = {}
-    # level-batched (graph) vs one launch per bucket, MBE log2 <= 16
+    peak, _ = _peaks()
+    # level-batched vs one launch per bucket, MBE log2 <= 16: each form with
+    # direct launches and replayed from a CUDA graph (so graph replay and
+    # batching are measured apart), the launch over all levels, and the
+    # autotuned configuration
     inst = synth.config_instance(2, 0)
     times = {}
-    for name, kw in (("batched", dict(batched=True, use_graph=True)),
-                     ("plain", dict(batched=False, use_graph=False))):
+    for name, kw in (("batched", dict(batched=1, use_graph=True)),
+                     ("batched_direct", dict(batched=1, use_graph=False)),
+                     ("plain", dict(batched=0, use_graph=False)),
+                     ("plain_graph", dict(batched=0, use_graph=True)),
+                     ("fused", dict(batched=2, use_graph=True)),
+                     ("tuned", dict(batched=1, use_graph=True, autotune_cache=TUNE_CACHE))):
         st = gb.UtilState(inst, "mbe", 16, ibound_mode="log2", **kw)
         st.bind()
+        if name == "tuned":
+            st.autotune()
+            tuned_cfg = st.launch_config()
         ms = []
         for k in range(3 + steps):
             st.run()
@@ -204,25 +215,36 @@ def secondary(torch, gb, synth, steps):
     out["mbe_er500"] = {"workload": "MBE Erdos-Renyi n=500, 1500 ternary tables, log2 bound 16",
                         "tasks": info["n_tasks"], "levels": info["n_levels"],
                         "util_entries": info["util_entries"],
-                        "batched_ms": times["batched"], "plain_ms": times["plain"],
-                        "batched_speedup": times["plain"] / times["batched"]}
-    # MPE, -log p in fp32, MBE i = 20
+                        "batched_ms": times["batched"], "batched_direct_ms": times["batched_direct"],
+                        "plain_ms": times["plain"], "plain_graph_ms": times["plain_graph"],
+                        "fused_ms": times["fused"], "tuned_ms": times["tuned"], "tuned_config": tuned_cfg,
+                        "batched_speedup": times["plain"] / times["batched"],
+                        "batched_speedup_both_graph": times["plain_graph"] / times["batched"],
+                        "batched_speedup_both_direct": times["plain"] / times["batched_direct"],
+                        "tuned_speedup_vs_plain_graph": times["plain_graph"] / times["tuned"]}
+    # MPE, -log p in fp32, MBE i = 20 (autotuned launch configuration)
     inst = synth.config_instance(3, 0)
-    st = gb.UtilState(inst, "mbe", 20, ibound_mode="sep", use_graph=True)
+    st = gb.UtilState(inst, "mbe", 20, ibound_mode="sep", use_graph=True, autotune_cache=TUNE_CACHE)
     st.bind()
+    st.autotune()
+    mpe_cfg = st.launch_config()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     ms = []
-    for k in range(2 + steps):
+    for k in range(3 + steps):
+        flush.fill_(k & 0xFF)
         st.run()
         st.sync()
-        if k >= 2:
+        if k >= 3:
             ms.append(st.times()[0])
     info = st.info()
     st.free()
+    del flush
     m = statistics.median(ms)
     out["mpe_bn200"] = {"workload": "MPE Bayesian network n=200, MBE i=20 (fp32 -log p)",
                         "util_entries": info["util_entries"], "util_ms": m,
                         "entries_per_s": info["util_entries"] / (m * 1e-3),
-                        "gbs": info["alg_bytes"] / (m * 1e-3) / 1e9}
+                        "gbs": info["alg_bytes"] / (m * 1e-3) / 1e9,
+                        "hbm_frac": info["alg_bytes"] / (m * 1e-3) / 1e9 / peak, "config": mpe_cfg}
     # repeated mini-bucket bounds under changing evidence (the bound inside a
     # search): one plan, util_condition + graph replay per bound, against
     # planning and binding a new state per bound (direct launches, the
@@ -269,7 +291,8 @@ def secondary(torch, gb, synth, steps):
     inst = synth.grid_mrf(12, 12, 4, seed=0, unary=False)
     st = gb.UtilState(inst, "sum", order="best", use_graph=True, autotune_cache=TUNE_CACHE)
     st.bind()
-    thr, rows = st.autotune()
+    st.autotune()
+    sum_cfg = st.launch_config()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     ms = []
     for k in range(3 + steps):
@@ -283,14 +306,60 @@ def secondary(torch, gb, synth, steps):
     st.free()
     del flush
     m = statistics.median(ms)
-    peak, _ = _peaks()
     gbs = info["alg_bytes"] / (m * 1e-3) / 1e9
     out["logz_mrf12x12"] = {"workload": "sum-product -log Z, 12x12 grid MRF, d=4, 264 pairwise tables (fp32)",
                             "util_entries": info["util_entries"], "util_ms": m,
                             "entries_per_s": info["util_entries"] / (m * 1e-3), "gbs": gbs,
-                            "hbm_frac": gbs / peak, "block_threads": thr, "rows_per_item": rows,
-                            "neg_log_z": logz}
+                            "hbm_frac": gbs / peak, "config": sum_cfg, "neg_log_z": logz}
+    out["shapes"] = shape_lines(torch, gb, synth, steps)
     out["serving"] = serve_bench(torch, gb, synth, int(os.environ.get("GPUBE_SERVE_REQUESTS", "2000")))
+    return out
+
+
+def time_util(torch, st, steps, flush=None):
+    """Median UTIL ms of a bound state over `steps` runs after 3 warm-up runs
+    (L2 flushed before each run when a flush buffer is given)."""
+    ms = []
+    for k in range(3 + steps):
+        if flush is not None:
+            flush.fill_(k & 0xFF)
+        st.run()
+        st.sync()
+        if k >= 3:
+            ms.append(st.times()[0])
+    return statistics.median(ms)
+
+
+def shape_lines(torch, gb, synth, steps):
+    """The other workload shapes, each autotuned: the 4x5 grid (exact BE,
+    min-fill), exact BE on the 60-variable prefix of the Bayesian network
+    (fp32), and the random-network, scale-free and grid generators of the
+    paper's experiments (Section 8.1 shapes, exact BE in the best order)."""
+    peak, _ = _peaks()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    cases = [("grid4x5_d4", synth.config_instance(0, 0), "minfill"),
+             ("bn200_prefix60_be", synth.bn_prefix(synth.config_instance(3, 0), 60), "minfill")]
+    for n, d, p1 in ((14, 8, 0.5), (12, 16, 0.3), (10, 32, 0.4), (8, 100, 0.4)):
+        cases.append((f"random_n{n}_d{d}", synth.random_network_wcsp(n, d, p1, seed=1), "best"))
+    for n, d in ((150, 4), (300, 2)):
+        cases.append((f"scalefree_n{n}_d{d}", synth.scale_free_wcsp(n, d, seed=1), "best"))
+    for r, c, d in ((20, 20, 2), (14, 14, 3), (9, 9, 6), (8, 8, 8), (6, 6, 16)):
+        cases.append((f"grid{r}x{c}_d{d}", synth.grid_wcsp(r, c, d, seed=1, unary=False), "best"))
+    out = {}
+    for name, inst, order in cases:
+        st = gb.UtilState(inst, "be", order=order, use_graph=True, autotune_cache=TUNE_CACHE)
+        st.bind()
+        st.autotune()
+        m = time_util(torch, st, steps, flush)
+        info = st.info()
+        cfg = st.launch_config()
+        st.free()
+        out[name] = {"n": inst.n, "width": info["induced_width"], "levels": info["n_levels"],
+                     "util_entries": info["util_entries"], "util_ms": m,
+                     "entries_per_s": info["util_entries"] / (m * 1e-3),
+                     "hbm_frac": info["alg_bytes"] / (m * 1e-3) / 1e9 / peak,
+                     "mode": cfg["batched"], "lo_target": cfg["lo_target"]}
+    del flush
     return out
 
 
@@ -555,7 +624,8 @@ def main():
     inst = synth.config_instance(1, seed=rank)  # one replica per rank
     st = gb.UtilState(inst, "be", order="best", use_graph=True, device=local, autotune_cache=TUNE_CACHE)
     st.bind(device=local)
-    threads, rows = st.autotune()  # launch shape measured on this instance (cached)
+    threads, rows = st.autotune()  # launch configuration measured on this instance (cached)
+    tuned = st.launch_config()
     info = st.info()
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -589,7 +659,8 @@ def main():
     tot_s = max_over_ranks(sum(step_ms) * 1e-3, dev)
     value = whole_job_rate(info["util_entries"], world, args.steps, tot_s)
     res = st.value()
-    n_launch_step = info["n_levels"] + 1  # one UTIL launch per level + the VALUE kernel
+    # UTIL launches of one step (one per level, or one over all levels) + the VALUE kernel
+    n_launch_step = (1 if tuned["batched"] == 2 else info["n_levels"]) + 1
 
     # roofline of the UTIL kernel: algorithmic bytes / its device time
     peak, peak_kind = _peaks()
@@ -598,8 +669,8 @@ def main():
     traffic = _traffic_per_launch()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
-                "alg_bytes_per_launch": info["alg_bytes"] / info["n_levels"],
-                "alg_bytes_per_step": info["alg_bytes"], "launches_per_step": info["n_levels"]}
+                "alg_bytes_per_launch": info["alg_bytes"] / (n_launch_step - 1),
+                "alg_bytes_per_step": info["alg_bytes"], "launches_per_step": n_launch_step - 1}
     st.free()
     del flush
 
@@ -613,7 +684,7 @@ def main():
         t0 = time.perf_counter()
         w = gb.WCSP(pk)
         r = gb.be_solve(w, order="best", arena=arena.data_ptr(), arena_bytes=arena.numel(),
-                        stream=stream.cuda_stream, device=local, block_threads=threads, rows_per_item=rows)
+                        stream=stream.cuda_stream, device=local, **tuned)
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_s.append(t1 - t0)
@@ -651,7 +722,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "buckets": info["n_tasks"], "levels": info["n_levels"],
-                           "block_threads": threads, "rows_per_item": rows,
+                           "block_threads": threads, "rows_per_item": rows, "launch": tuned,
                            "util_entries_per_step": info["util_entries"],
                            "l2": "flushed between steps (512 MB write)",
                            "parallelism": f"replicas x{world}", "bound": res.bound},

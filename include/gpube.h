@@ -113,7 +113,10 @@ typedef struct solve_opts {
     const int32_t *parent;     /* [n] host pseudo-tree (-1 = root) for ORDER_PSEUDOTREE  */
     int32_t ibound_mode;       /* enum gpube_ibound_mode (MBE)                           */
     int32_t batched;           /* 1: one persistent launch per elimination-tree level;
-                                  0: one launch per (mini-)bucket                        */
+                                  0: one launch per (mini-)bucket;
+                                  2: one persistent launch over every level, whose CTAs
+                                     wait on the device (bounded, GPUBE_ETIMEDOUT) for the
+                                     buckets that produce a bucket's inputs              */
     int32_t use_graph;         /* 1: capture the launch sequence once in a CUDA graph    */
     int32_t block_threads;     /* UTIL kernel CTA size (64..1024, multiple of 32); 0 = auto */
     int32_t rows_per_item;     /* separator rows of one work item per thread; 0 = auto  */
@@ -128,6 +131,8 @@ typedef struct solve_opts {
     const int32_t *evidence_vars; /* [n_evidence_vars] host: variables that util_condition
                                   may clamp on this plan (distinct), or NULL             */
     int32_t n_evidence_vars;
+    int32_t pipeline;          /* 0: group inputs prefetched by the cp.async pipeline where a
+                                  task allows it; -1: register variants only              */
 } solve_opts;
 
 /* Result of a solve.  assignment, when non-NULL, is caller-owned host memory
@@ -272,11 +277,32 @@ int util_sync(util_state *s);
  * host buffers (either may be NULL); synchronous. */
 int util_fetch_table(util_state *s, int32_t t, void *cost_host, uint8_t *arg_host);
 
-/* Measure candidate launch parameters (CTA size, rows per item) on this
- * state's own UTIL phase, keep the fastest, and record them in
- * opts.autotune_cache when given.  Writes the chosen values to *threads and
- * *rows_per_item (either may be NULL). */
+/* The launch configuration of a state (what util_autotune chooses). */
+typedef struct gpube_launch_config {
+    int32_t block_threads;     /* UTIL kernel CTA size                                    */
+    int32_t rows_per_item;     /* separator rows of one work item per thread (target)     */
+    int32_t lo_target;         /* minimum extent of a work item's inner row block         */
+    int32_t stage_max_entries; /* tables up to this many entries staged in shared memory (0: none) */
+    int32_t pipeline;          /* 1: a task's group input is prefetched by the per-thread
+                                  cp.async pipeline (4-12 groups in flight) where the task
+                                  allows it; 0: register variants (1-2 groups in flight)  */
+    int32_t launch_mode;       /* solve_opts.batched: 0 per bucket, 1 per level, 2 fused  */
+} gpube_launch_config;
+
+/* Measure candidate launch configurations on this state's own UTIL phase and
+ * keep the fastest: CTA size x rows per item, then the lo extent target, the
+ * launch mode (per level or one launch over all levels; a per-bucket state
+ * keeps its mode), the staging limit and the group-input pipeline, each
+ * varied around the best so far, then the launch shape once more.  Changing
+ * the lo target or the staging limit re-shapes the tasks and rebuilds the
+ * offset tables in the bound arena (candidates that do not fit it are
+ * skipped); the tables computed by later runs are unchanged (bit for bit for
+ * integer costs).  The choice is appended to opts.autotune_cache when given
+ * and read back from it for the same plan.  Writes the chosen CTA size and
+ * rows per item to *threads and *rows_per_item (either may be NULL); the
+ * whole configuration is available from util_launch_config. */
 int util_autotune(util_state *s, int32_t *threads, int32_t *rows_per_item);
+int util_launch_config(const util_state *s, gpube_launch_config *out);
 
 /* Conditioning: clamp variables to values for the following runs of the same
  * plan, without planning or binding again (evidence in a Bayesian network,
@@ -354,6 +380,13 @@ int util_bucket_scratch_bytes(int32_t m, const int32_t *sep_dom, int32_t d, int3
  * status, not a hang or a trap; the context stays usable), GPUBE_ECUDA on a
  * CUDA error.  Synchronous on stream.  The paper has no counterpart. */
 int util_selftest_wait(uint64_t timeout_ns, void *stream);
+
+/* Diagnostic: one thread runs the wait of a launch over all levels
+ * (solve_opts.batched = 2) for a producing bucket that never completes.
+ * Returns GPUBE_ETIMEDOUT after about timeout_ns, GPUBE_ECUDA on a CUDA
+ * error; the context stays usable.  Synchronous on stream.  The paper has
+ * no counterpart. */
+int util_selftest_dep_wait(uint64_t timeout_ns, void *stream);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -99,10 +99,13 @@ class WCSP:
             self.h = None
 
 
+LAUNCH_MODES = {"bucket": 0, "level": 1, "fused": 2}
+
+
 def make_opts(order="minfill", order_array=None, parent=None, ibound_mode="sep", batched=True,
               use_graph=False, block_threads=0, rows_per_item=0, lo_target=0,
               stage_max_entries=0, arena=None, arena_bytes=0, stream=None,
-              autotune_cache=None, device=0, evidence_vars=None):
+              autotune_cache=None, device=0, evidence_vars=None, pipeline=True):
     o = _abi.SolveOpts()
     lib().solve_opts_init(C.byref(o))
     o.order_kind = ORDERS[order] if isinstance(order, str) else int(order)
@@ -118,7 +121,9 @@ def make_opts(order="minfill", order_array=None, parent=None, ibound_mode="sep",
         keep.append(p)
         o.parent = _ptr(p)
     o.ibound_mode = IBOUND[ibound_mode] if isinstance(ibound_mode, str) else int(ibound_mode)
-    o.batched = 1 if batched else 0
+    # launch mode: False / 0 = one launch per bucket, True / 1 = one per
+    # elimination-tree level, "fused" / 2 = one launch over all levels
+    o.batched = LAUNCH_MODES[batched] if isinstance(batched, str) else int(batched)
     o.use_graph = 1 if use_graph else 0
     o.block_threads = int(block_threads)
     o.rows_per_item = int(rows_per_item)
@@ -132,6 +137,7 @@ def make_opts(order="minfill", order_array=None, parent=None, ibound_mode="sep",
         keep.append(b)
         o.autotune_cache = b
     o.device = int(device)
+    o.pipeline = 0 if pipeline else -1
     if evidence_vars is not None and len(evidence_vars):
         ev = _i32(evidence_vars)
         keep.append(ev)
@@ -270,6 +276,9 @@ class UtilState:
         torch = _torch()
         need = self.info()["arena_bytes"]
         if arena is None:
+            # headroom for the re-shaped layouts util_autotune tries (a smaller
+            # lo extent enlarges the per-group offset tables)
+            need += min(need // 8, 256 << 20) + (4 << 20)
             arena = torch.empty(max(need, 256), dtype=torch.uint8, device=f"cuda:{device}")
         self.arena_tensor = arena
         st = current_stream(device) if stream is None else stream
@@ -320,6 +329,15 @@ class UtilState:
         a, b = C.c_int32(), C.c_int32()
         _check(lib().util_autotune(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def launch_config(self):
+        """The state's launch configuration (``util_launch_config``) as the
+        keyword options that reproduce it in a solve."""
+        c = _abi.LaunchConfig()
+        _check(lib().util_launch_config(self.h, C.byref(c)))
+        return {"block_threads": c.block_threads, "rows_per_item": c.rows_per_item, "lo_target": c.lo_target,
+                "stage_max_entries": c.stage_max_entries if c.stage_max_entries > 0 else -1,
+                "pipeline": bool(c.pipeline), "batched": c.launch_mode}
 
     def free(self):
         if getattr(self, "h", None) and _abi._lib is not None:

@@ -31,7 +31,12 @@ class SolveOpts(C.Structure):
                 ("lo_target", C.c_int32), ("stage_max_entries", C.c_int32),
                 ("arena", C.c_void_p), ("arena_bytes", C.c_size_t), ("stream", C.c_void_p),
                 ("autotune_cache", C.c_char_p), ("device", C.c_int32),
-                ("evidence_vars", i32p), ("n_evidence_vars", C.c_int32)]
+                ("evidence_vars", i32p), ("n_evidence_vars", C.c_int32), ("pipeline", C.c_int32)]
+
+
+class LaunchConfig(C.Structure):
+    _fields_ = [("block_threads", C.c_int32), ("rows_per_item", C.c_int32), ("lo_target", C.c_int32),
+                ("stage_max_entries", C.c_int32), ("pipeline", C.c_int32), ("launch_mode", C.c_int32)]
 
 
 class SolveResult(C.Structure):
@@ -81,6 +86,7 @@ SIGNATURES = {
     "util_sync": (C.c_int, [C.c_void_p]),
     "util_fetch_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, u8p]),
     "util_autotune": (C.c_int, [C.c_void_p, i32p, i32p]),
+    "util_launch_config": (C.c_int, [C.c_void_p, C.POINTER(LaunchConfig)]),
     "util_last_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "util_bucket": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, i32p, C.c_int32, C.c_int32,
                               C.POINTER(C.c_void_p), i32p, i32p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -90,6 +96,7 @@ SIGNATURES = {
     "util_bucket_scratch_bytes": (C.c_int, [C.c_int32, i32p, C.c_int32, C.c_int32, i32p, i32p,
                                             C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "util_selftest_wait": (C.c_int, [C.c_uint64, C.c_void_p]),
+    "util_selftest_dep_wait": (C.c_int, [C.c_uint64, C.c_void_p]),
     "srv_create": (C.c_int, [C.c_size_t, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
                              C.POINTER(C.c_void_p)]),
     "srv_submit": (C.c_int64, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, i32p,

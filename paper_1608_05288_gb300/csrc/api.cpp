@@ -299,6 +299,8 @@ void gpube_layout(util_state *s)
     D.expand = c.take(sizeof(ExpandDev) * nt, 16);
     D.exp_prefix = c.take(8 * (nt + 1), 16);
     D.pool = c.take(4 * D.n_pool, 16);
+    D.dep_off = c.take(4 * (nt + 1), 16);
+    D.deps = c.take(4 * std::max<size_t>(D.n_in, 1), 16);
     s->desc_bytes = c.off - s->desc_off;
     const ValuePlanH &V = P.value;
     s->value_off = al(c.off, 16);
@@ -311,7 +313,9 @@ void gpube_layout(util_state *s)
     D.evals = c.take(sizeof(ValueTerm) * V.evals.size(), 16);
     D.roots = c.take(8 * V.roots.size(), 16);
     s->value_bytes = c.off - s->value_off;
-    const size_t n_counters = std::max<size_t>(std::max<size_t>(nt, P.n_levels), 1);
+    // queue heads (one per launch), or one head and a completion count per
+    // task for a launch over all levels
+    const size_t n_counters = std::max<size_t>(std::max<size_t>(nt + 1, P.n_levels), 1);
     s->counters_off = c.take(4 * n_counters, 256);
     s->status_off = c.take(8, 16);
     s->result_off = s->status_off + 8;
@@ -398,7 +402,11 @@ extern "C" int util_plan(wcsp *w, int32_t kind, int32_t i_bound, const int32_t *
     }
     s->opts = o;
     s->opts.evidence_vars = nullptr;  // not kept: the caller owns the array
-    s->batched = o.batched != 0;
+    if (o.batched < kLaunchPerTask || o.batched > kLaunchFused) {
+        delete s;
+        return set_error(GPUBE_EINVAL, "batched must be 0 (per bucket), 1 (per level) or 2 (all levels in one launch)");
+    }
+    s->launch_mode = o.batched;
     s->use_graph = o.use_graph != 0;
     s->device = o.device;
     if (o.block_threads) {
@@ -571,7 +579,7 @@ int gpube_build_descriptors(util_state *s)
         x.n_gi = T.n_gi;
         // one global group input, at most 3 inputs, a fixed-domain variant:
         // prefetch that input with the per-thread cp.async pipeline
-        x.pipe = (x.F <= 3 && T.d >= 2 && T.d <= 8 && T.n_gi - T.n_lo == 1 && T.stage_off[T.n_lo] < 0 &&
+        x.pipe = (P.allow_pipe && x.F <= 3 && T.d >= 2 && T.d <= 8 && T.n_gi - T.n_lo == 1 && T.stage_off[T.n_lo] < 0 &&
                   T.G > 1)
                      ? 1
                      : 0;
@@ -604,31 +612,33 @@ int gpube_build_descriptors(util_state *s)
         occ[smem] = nb;
         return nb;
     };
-    auto add_launch = [&](int first, int count, int counter_idx) {
-        LaunchDev L{};
-        L.tasks = td_dev + first;
-        L.prefix = pre_dev + pp;
-        L.n_tasks = count;
+    // shared memory of a launch over tasks [first, first + count): staged
+    // tables | the item's A rows | pipeline slots and four per-u partial sums
+    // per thread (cp.async path)
+    auto launch_smem = [&](int first, int count, LaunchDev &L) {
         int smem = 0, pipe_b = 0;
-        double work = 0.0;  // thread-rows of the launch, idle lanes of partial lo chunks included
         for (int i = 0; i < count; ++i) {
             const TaskDev &x = td[first + i];
             smem = std::max(smem, x.stage_bytes);
             if (x.pipe) pipe_b = std::max(pipe_b, pipe_bytes_per_thread(x.d));
-            work += static_cast<double>(x.nlc) * NT * x.G * x.R0;
         }
-        // shared memory: staged tables | the item's A rows | pipeline slots
-        // and four per-u partial sums per thread (cp.async path)
         L.arows_off = static_cast<int32_t>(al(smem, 16));
         L.pipe_off = L.arows_off + (pipe_b ? kMaxPipeRows * 16 : 0);
         if (pipe_b) smem = L.pipe_off + NT * pipe_b;
-        const int64_t cap = static_cast<int64_t>(blocks_per_sm(smem)) * s->num_sms;
-        // whole waves: items of about equal size, about a multiple of the
-        // resident CTAs, near rows_per_item rows per thread
+        return smem;
+    };
+    // work items of tasks [first, first + count) for cap resident CTAs: whole
+    // waves of items of about equal size, near rows_per_item rows per thread;
+    // their first items go to first_item[i], numbered from *tot on
+    auto size_items = [&](int first, int count, int64_t cap, int64_t *tot, int32_t *first_item) {
+        double work = 0.0;  // thread-rows, idle lanes of partial lo chunks included
+        for (int i = 0; i < count; ++i) {
+            const TaskDev &x = td[first + i];
+            work += static_cast<double>(x.nlc) * NT * x.G * x.R0;
+        }
         const double pref = std::max(s->cfg.rows_per_item, 1);
         const double waves = std::max(1.0, std::round(work / (static_cast<double>(cap) * NT * pref)));
         const double rows_per_thread = work / (waves * cap * NT);
-        int64_t tot = 0;
         for (int i = 0; i < count; ++i) {
             TaskDev &x = td[first + i];
             const int64_t hc = std::llround(rows_per_thread / std::max(x.R0, 1));
@@ -637,12 +647,24 @@ int gpube_build_descriptors(util_state *s)
             const int64_t items = static_cast<int64_t>(x.nlc) * ((x.G + x.hc - 1) / x.hc);
             if (items > INT32_MAX / 2) return set_error(GPUBE_ENOMEM, "a task has too many work items");
             x.n_items = static_cast<int32_t>(items);
-            pre[pp + i] = static_cast<int32_t>(tot);
-            tot += items;
+            first_item[i] = static_cast<int32_t>(*tot);
+            *tot += items;
         }
+        if (*tot > INT32_MAX / 2) return set_error(GPUBE_ENOMEM, "launch has too many work items");
+        return GPUBE_OK;
+    };
+    auto add_launch = [&](int first, int count, int counter_idx) {
+        LaunchDev L{};
+        L.tasks = td_dev + first;
+        L.prefix = pre_dev + pp;
+        L.n_tasks = count;
+        const int smem = place_prefix_smem(L, launch_smem(first, count, L));
+        const int64_t cap = static_cast<int64_t>(blocks_per_sm(smem)) * s->num_sms;
+        int64_t tot = 0;
+        int rc = size_items(first, count, cap, &tot, pre + pp);
+        if (rc) return rc;
         pre[pp + count] = static_cast<int32_t>(tot);
         pp += count + 1;
-        if (tot > INT32_MAX / 2) return set_error(GPUBE_ENOMEM, "launch has too many work items");
         L.total_items = static_cast<int32_t>(tot);
         L.counter = counters + counter_idx;
         L.status = status;
@@ -652,16 +674,64 @@ int gpube_build_descriptors(util_state *s)
         s->launch_smem.push_back(smem);
         return GPUBE_OK;
     };
-    if (s->batched) {
+    s->n_zero = 1;
+    if (s->launch_mode == kLaunchFused) {
+        // one persistent launch over all levels: tasks in level order, each
+        // level's items sized for the launch's resident CTAs, a task's CTAs
+        // wait on the device for the tasks that produce its inputs
+        LaunchDev L{};
+        L.tasks = td_dev;
+        L.prefix = pre_dev + pp;
+        L.n_tasks = static_cast<int32_t>(nt);
+        const int smem = place_prefix_smem(L, launch_smem(0, static_cast<int>(nt), L));
+        const int64_t cap = static_cast<int64_t>(blocks_per_sm(smem)) * s->num_sms;
+        int64_t tot = 0;
+        for (int l = 0; l < P.n_levels; ++l) {
+            const int first = P.level_off[l], count = P.level_off[l + 1] - P.level_off[l];
+            int rc = size_items(first, count, cap, &tot, pre + pp + first);
+            if (rc) return rc;
+        }
+        pre[pp + nt] = static_cast<int32_t>(tot);
+        pp += nt + 1;
+        int32_t *doff = reinterpret_cast<int32_t *>(at(D.dep_off));
+        int32_t *dl = reinterpret_cast<int32_t *>(at(D.deps));
+        size_t nd = 0;
+        for (size_t i = 0; i < nt; ++i) {
+            doff[i] = static_cast<int32_t>(nd);
+            const size_t nd0 = nd;
+            for (int fid : P.tasks[P.level_order[i]].inputs) {
+                const int pt = P.funcs[fid].task;
+                if (pt < 0) continue;
+                const int ps = slot[pt];
+                if (static_cast<size_t>(ps) >= i)
+                    return set_error(GPUBE_EINVAL, "internal: task %d depends on a later task", static_cast<int>(i));
+                if (std::find(dl + nd0, dl + nd, ps) == dl + nd) dl[nd++] = ps;
+            }
+        }
+        doff[nt] = static_cast<int32_t>(nd);
+        L.total_items = static_cast<int32_t>(tot);
+        L.counter = counters;
+        L.done = counters + 1;
+        L.dep_off = reinterpret_cast<const int32_t *>(B + D.dep_off);
+        L.deps = reinterpret_cast<const int32_t *>(B + D.deps);
+        L.status = status;
+        L.top_k = w.top_k;
+        s->launches.push_back(L);
+        s->launch_grid.push_back(static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(tot, cap))));
+        s->launch_smem.push_back(smem);
+        s->n_zero = static_cast<int32_t>(nt + 1);
+    } else if (s->launch_mode == kLaunchPerLevel) {
         for (int l = 0; l < P.n_levels; ++l) {
             int rc = add_launch(P.level_off[l], P.level_off[l + 1] - P.level_off[l], l);
             if (rc) return rc;
         }
+        s->n_zero = std::max(P.n_levels, 1);
     } else {
         for (size_t t = 0; t < nt; ++t) {
             int rc = add_launch(slot[t], 1, static_cast<int>(t));
             if (rc) return rc;
         }
+        s->n_zero = static_cast<int32_t>(std::max<size_t>(nt, 1));
     }
     // expansion plan
     ExpandDev *ex = reinterpret_cast<ExpandDev *>(at(D.expand));
@@ -818,12 +888,14 @@ extern "C" int util_bind(util_state *s, void *arena, size_t arena_bytes, void *s
         }
         s->base = static_cast<unsigned char *>(p);
         s->owns_arena = true;
+        s->arena_cap = s->arena_bytes;
     } else {
         if (arena_bytes < s->arena_bytes)
             return set_error(GPUBE_ENOMEM, "arena of %zu bytes, the plan needs %zu", arena_bytes, s->arena_bytes);
         if (reinterpret_cast<uintptr_t>(arena) % 256)
             return set_error(GPUBE_EINVAL, "arena must be 256-byte aligned");
         s->base = static_cast<unsigned char *>(arena);
+        s->arena_cap = arena_bytes;
     }
     s->stream = static_cast<cudaStream_t>(stream);
     // (timing events and the capture stream are created when first needed)
@@ -859,8 +931,7 @@ static int ensure_events(util_state *s)
 
 int gpube_enqueue_util(util_state *s, cudaStream_t st)
 {
-    const size_t n_counters = std::max<size_t>(s->launches.size(), 1);
-    CUDA_TRY(cudaMemsetAsync(s->base + s->counters_off, 0, 4 * n_counters, st));
+    CUDA_TRY(cudaMemsetAsync(s->base + s->counters_off, 0, 4 * static_cast<size_t>(s->n_zero), st));
     // consecutive levels: each launch may be scheduled while the previous one
     // drains (it waits for it before reading any table)
     for (size_t i = 0; i < s->launches.size(); ++i)
@@ -1048,13 +1119,99 @@ extern "C" void util_state_free(util_state *s)
 }
 
 // ---------------------------------------------------------------- autotune
+// The launch configuration of a state: the kernel launch shape (CTA size,
+// rows per work item), the work decomposition (lo extent target, staging
+// limit), the group-input pipeline and the launch mode.
+namespace {
+struct TuneCfg {
+    int32_t threads, rows, lo, stage, pipe, mode;
+    bool operator==(const TuneCfg &o) const
+    {
+        return threads == o.threads && rows == o.rows && lo == o.lo && stage == o.stage && pipe == o.pipe &&
+               mode == o.mode;
+    }
+};
+
+TuneCfg current_cfg(const util_state *s)
+{
+    return TuneCfg{s->cfg.threads, s->cfg.rows_per_item, s->plan.lo_target, s->plan.stage_max_entries,
+                   s->plan.allow_pipe ? 1 : 0, s->launch_mode};
+}
+
+// Expand the offset tables of a bound state on its stream (after the
+// descriptors are uploaded).
+int expand_tables(util_state *s)
+{
+    const DescLayout &D = layout_of(s);
+    CUDA_TRY(launch_expand(reinterpret_cast<const ExpandDev *>(s->base + D.expand),
+                           reinterpret_cast<const int64_t *>(s->base + D.exp_prefix),
+                           static_cast<int>(s->plan.tasks.size()),
+                           reinterpret_cast<const int64_t *>(s->host_blob.data() + (D.exp_prefix - s->desc_off))
+                               [s->plan.tasks.size()],
+                           reinterpret_cast<const int32_t *>(s->base + D.pool), s->num_sms, s->stream));
+    return GPUBE_OK;
+}
+}  // namespace
+
+// Apply a configuration to a bound state.  A new lo target or staging limit
+// re-shapes the tasks (decomposition, input classes, staged tables) and lays
+// the arena out again: the original tables, bucket functions and argmin
+// tables keep their offsets (they come first and do not depend on the
+// shape); the offset tables, descriptors and value plan after them are
+// rebuilt and expanded again.  ENOMEM (state unchanged) when the new layout
+// does not fit the bound arena.
+static int apply_cfg(util_state *s, const TuneCfg &c)
+{
+    Plan &P = s->plan;
+    const TuneCfg old = current_cfg(s);
+    const bool reshape = c.lo != P.lo_target || c.stage != P.stage_max_entries;
+    if (reshape) {
+        P.lo_target = c.lo;
+        P.stage_max_entries = c.stage;
+        shape_tasks(*s->w, P);
+        gpube_layout(s);
+        if (s->arena_bytes > s->arena_cap) {
+            P.lo_target = old.lo;
+            P.stage_max_entries = old.stage;
+            shape_tasks(*s->w, P);
+            gpube_layout(s);
+            return set_error(GPUBE_ENOMEM, "the re-shaped plan does not fit the bound arena");
+        }
+    }
+    s->cfg.threads = c.threads;
+    s->cfg.rows_per_item = c.rows;
+    P.allow_pipe = c.pipe != 0;
+    s->launch_mode = c.mode;
+    int rc = upload_descriptors(s);
+    if (rc) return rc;
+    if (reshape) {
+        // the status word moved with the layout: it starts at zero again
+        CUDA_TRY(cudaMemsetAsync(s->base + s->status_off, 0, 8, s->stream));
+        return expand_tables(s);
+    }
+    return GPUBE_OK;
+}
+
 static std::string tune_key(const util_state *s)
 {
     const Plan &P = s->plan;
     std::ostringstream k;
     k << "k" << P.kind << "_t" << P.tasks.size() << "_l" << P.n_levels << "_e" << P.util_entries << "_c"
-      << s->ktype << "_b" << (s->batched ? 1 : 0);
+      << s->ktype << "_w" << P.width << "_m" << (s->launch_mode == kLaunchPerTask ? 0 : 1);
     return k.str();
+}
+
+extern "C" int util_launch_config(const util_state *s, gpube_launch_config *out)
+{
+    if (!s || !out) return set_error(GPUBE_EINVAL, "null argument");
+    const TuneCfg c = current_cfg(s);
+    out->block_threads = c.threads;
+    out->rows_per_item = c.rows;
+    out->lo_target = c.lo;
+    out->stage_max_entries = c.stage;
+    out->pipeline = c.pipe;
+    out->launch_mode = c.mode;
+    return GPUBE_OK;
 }
 
 extern "C" int util_autotune(util_state *s, int32_t *threads, int32_t *rows_per_item)
@@ -1062,57 +1219,119 @@ extern "C" int util_autotune(util_state *s, int32_t *threads, int32_t *rows_per_
     if (!s || !s->bound) return set_error(GPUBE_EINVAL, "state is not bound");
     const std::string key = tune_key(s);
     const char *cache = s->opts.autotune_cache;
+    auto report = [&]() {
+        if (threads) *threads = s->cfg.threads;
+        if (rows_per_item) *rows_per_item = s->cfg.rows_per_item;
+        return GPUBE_OK;
+    };
     if (cache) {
         std::ifstream in(cache);
-        std::string k;
-        int th, rp;
-        double ms;
-        while (in >> k >> th >> rp >> ms)
-            if (k == key) {
-                s->cfg.threads = th;
-                s->cfg.rows_per_item = rp;
-                int rc = upload_descriptors(s);
+        std::string line;
+        while (std::getline(in, line)) {
+            std::istringstream ls(line);
+            std::string k;
+            TuneCfg c{};
+            double ms;
+            if (ls >> k >> c.threads >> c.rows >> c.lo >> c.stage >> c.pipe >> c.mode >> ms && k == key) {
+                int rc = apply_cfg(s, c);
+                if (rc == GPUBE_ENOMEM) break;  // measured with a larger arena: tune here
                 if (rc) return rc;
-                if (threads) *threads = th;
-                if (rows_per_item) *rows_per_item = rp;
-                return GPUBE_OK;
-            }
-    }
-    const int cand_t[] = {128, 256, 512};
-    const int cand_r[] = {16, 32, 64, 128, 256};
-    LaunchCfg best = s->cfg;
-    double best_ms = 1e30;
-    for (int th : cand_t)
-        for (int rp : cand_r) {
-            s->cfg.threads = th;
-            s->cfg.rows_per_item = rp;
-            int rc = upload_descriptors(s);
-            if (rc) return rc;
-            double tot = 0.0;
-            for (int rep = 0; rep < 3; ++rep) {
-                rc = util_run(s);
-                if (rc) return rc;
-                rc = util_sync(s);
-                if (rc) return rc;
-                double ms;
-                util_last_times(s, &ms, nullptr);
-                if (rep > 0) tot += ms;
-            }
-            if (tot < best_ms) {
-                best_ms = tot;
-                best = s->cfg;
+                return report();
             }
         }
-    s->cfg = best;
-    int rc = upload_descriptors(s);
+    }
+    // time one configuration: the mean of two runs after one warm-up run
+    auto measure = [&](const TuneCfg &c, double *ms) {
+        int rc = apply_cfg(s, c);
+        if (rc) return rc;
+        double tot = 0.0;
+        for (int rep = 0; rep < 3; ++rep) {
+            rc = util_run(s);
+            if (!rc) rc = util_sync(s);
+            if (rc) return rc;
+            double t;
+            util_last_times(s, &t, nullptr);
+            if (rep > 0) tot += t;
+        }
+        *ms = tot / 2;
+        return GPUBE_OK;
+    };
+    TuneCfg best = current_cfg(s);
+    double best_ms = 1e30;
+    std::vector<TuneCfg> seen;
+    // coordinate descent: each stage varies one part of the configuration
+    // around the best one so far (a candidate already timed is skipped)
+    auto try_all = [&](const std::vector<TuneCfg> &cands) {
+        for (const TuneCfg &c : cands) {
+            if (std::find(seen.begin(), seen.end(), c) != seen.end()) continue;
+            seen.push_back(c);
+            double ms;
+            int rc = measure(c, &ms);
+            if (rc == GPUBE_ENOMEM) continue;  // does not fit the bound arena
+            if (rc) return rc;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        return GPUBE_OK;
+    };
+    const int cand_t[] = {128, 256, 512};
+    const int cand_r[] = {16, 32, 64, 128, 256};
+    auto shapes = [&]() {
+        std::vector<TuneCfg> v;
+        for (int th : cand_t)
+            for (int rp : cand_r) {
+                TuneCfg c = best;
+                c.threads = th;
+                c.rows = rp;
+                v.push_back(c);
+            }
+        return v;
+    };
+    int rc = try_all(shapes());
+    if (!rc) {  // lo extent target of the work decomposition
+        std::vector<TuneCfg> v;
+        for (int lo : {128, 256, 512, 1024, 2048}) {
+            TuneCfg c = best;
+            c.lo = lo;
+            v.push_back(c);
+        }
+        rc = try_all(v);
+    }
+    if (!rc && s->plan.n_levels > 1) {  // one launch per level, or one over all levels
+        std::vector<TuneCfg> v;
+        for (int mode : {kLaunchPerLevel, kLaunchFused}) {
+            TuneCfg c = best;
+            c.mode = mode;
+            v.push_back(c);
+        }
+        if (s->launch_mode != kLaunchPerTask) rc = try_all(v);
+    }
+    if (!rc) {  // staging limit (0: no table staged) and the group-input pipeline
+        std::vector<TuneCfg> v;
+        for (int st : {0, 1024, 4096}) {
+            TuneCfg c = best;
+            c.stage = st;
+            v.push_back(c);
+        }
+        rc = try_all(v);
+        if (!rc) {
+            TuneCfg c = best;
+            c.pipe = 1 - c.pipe;
+            rc = try_all({c});
+        }
+    }
+    if (!rc) rc = try_all(shapes());  // the launch shape again, for the chosen decomposition
+    if (rc) return rc;
+    rc = apply_cfg(s, best);
     if (rc) return rc;
     if (cache) {
         std::ofstream out(cache, std::ios::app);
-        out << key << " " << best.threads << " " << best.rows_per_item << " " << best_ms / 2 << "\n";
+        out << key << " " << best.threads << " " << best.rows << " " << best.lo << " " << best.stage << " "
+            << best.pipe << " " << best.mode << " " << best_ms << "\n";
     }
-    if (threads) *threads = best.threads;
-    if (rows_per_item) *rows_per_item = best.rows_per_item;
-    return GPUBE_OK;
+    return report();
 }
 
 // ---------------------------------------------------------- one-call solvers
@@ -1251,7 +1470,7 @@ extern "C" int util_bucket(int32_t cost_type, int32_t top_k, int32_t m, const in
     P.level_off = {0, 1};
     shape_tasks(w, P);
     gpube_layout(&s);
-    s.batched = false;
+    s.launch_mode = kLaunchPerTask;
     s.use_graph = false;
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));

@@ -93,6 +93,16 @@ constexpr int pipe_bytes_per_thread(int d) { return (pipe_depth(d) + 4) * 4 * d;
 
 // One kernel launch: a list of tasks whose work items are handed out by an
 // atomic counter (a device-side work queue).
+//
+// A launch over every level of a run (done != nullptr) lists its tasks in
+// level order; a CTA that takes an item of task t first waits until every
+// task t depends on (its inputs' producers, deps[dep_off[t] .. dep_off[t+1]),
+// all earlier in the list) has completed all of its items, counted in
+// done[].  Items are taken in increasing order by CTAs that are running, and
+// a task depends only on earlier tasks, so the item with the lowest index not
+// yet completed never waits: the launch always progresses.  Each wait is
+// bounded; on expiry the CTA sets the status word and leaves, and the others
+// see the status and leave too.
 struct LaunchDev {
     const TaskDev *tasks;
     const int32_t *prefix;  // [n_tasks + 1] first work item of each task
@@ -103,8 +113,35 @@ struct LaunchDev {
     uint32_t top_k;         // WCSP saturation value
     int32_t pipe_off;       // byte offset of the cp.async pipeline area in shared memory
     int32_t arows_off;      // byte offset of the item's A rows (cp.async path) in shared memory
-    int32_t pad;
+    int32_t prefix_smem;    // byte offset of a shared-memory copy of prefix, -1 = none (read it
+                            // from global memory)
+    int32_t *done;          // [n_tasks] completed items per task, zeroed before the launch; nullptr:
+                            // a launch whose tasks depend on no task of the same launch
+    const int32_t *dep_off; // [n_tasks + 1]
+    const int32_t *deps;    // producer tasks (indices into tasks), each below the consumer's index
 };
+
+// A launch's prefix array is copied to shared memory (after the launch's
+// other shared-memory areas, which end at byte smem) when it is at most this
+// large: the task of each work item is then found by a binary search in
+// shared memory instead of a chain of dependent global loads.  Returns the
+// launch's shared-memory size.
+constexpr int kPrefixSmemMax = 16384;
+inline int place_prefix_smem(LaunchDev &L, int smem)
+{
+    const int bytes = (L.n_tasks + 1) * 4;
+    if (bytes > kPrefixSmemMax) {
+        L.prefix_smem = -1;
+        return smem;
+    }
+    L.prefix_smem = (smem + 15) / 16 * 16;
+    return L.prefix_smem + bytes;
+}
+
+// Launch modes of a run (solve_opts.batched).
+constexpr int kLaunchPerTask = 0;   // one launch per (mini-)bucket
+constexpr int kLaunchPerLevel = 1;  // one launch per elimination-tree level
+constexpr int kLaunchFused = 2;     // one launch for every level, dependencies waited for on the device
 
 // Compact plan of one task, expanded into its A and B tables on the device.
 struct alignas(16) ExpandDev {

@@ -113,6 +113,8 @@ struct Plan {
     int32_t lo_target = 2048;
     int32_t stage_max_entries = 4096;
     int32_t stage_max_bytes = 32768;
+    bool allow_pipe = true;   // group runs prefetched by the per-thread cp.async pipeline (KP groups in
+                              // flight) where a task allows it; false: register variants (1-2 groups)
     size_t peak_live_bytes = 0;
     ValuePlanH value;
 };
@@ -166,7 +168,7 @@ double now_ms();
 
 // Byte offsets of the descriptor and value regions of a state's arena.
 struct DescLayout {
-    size_t taskdev = 0, indev = 0, prefix = 0, expand = 0, exp_prefix = 0, pool = 0;
+    size_t taskdev = 0, indev = 0, prefix = 0, expand = 0, exp_prefix = 0, pool = 0, dep_off = 0, deps = 0;
     size_t lev_off = 0, vorder = 0, vinfo = 0, terms = 0, vvars = 0, vstrides = 0, evals = 0, roots = 0;
     size_t n_in = 0, n_prefix = 0, n_pool = 0;
 };
@@ -183,7 +185,9 @@ struct util_state {
     gpube::Plan plan;
     gpube::LaunchCfg cfg;
     solve_opts opts{};
-    bool batched = true, use_graph = true;
+    int launch_mode = 1;          // kLaunchPerTask / kLaunchPerLevel / kLaunchFused
+    bool use_graph = true;
+    int32_t n_zero = 1;           // work-area ints cleared before each run (queue heads, completion counts)
     double plan_ms = 0.0;
     // layout (byte offsets from the arena base)
     size_t upload_bytes = 0;     // originals, packed first
@@ -191,6 +195,7 @@ struct util_state {
     size_t value_off = 0, value_bytes = 0; // value plan region
     size_t work_off = 0;         // counters + status + result
     size_t arena_bytes = 0;
+    size_t arena_cap = 0;         // bytes of the bound arena (a re-shaped plan must fit in it)
     // device binding
     int device = 0;
     unsigned char *base = nullptr;

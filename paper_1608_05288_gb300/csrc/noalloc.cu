@@ -170,7 +170,7 @@ extern "C" int util_bucket_noalloc(int32_t cost_type, int32_t top_k, int32_t m, 
                          "util_bucket_noalloc: this bucket needs %zu bytes of scratch, the fixed scratch holds %zu "
                          "(use util_bucket)",
                          s.arena_bytes, kNoAllocScratchBytes);
-    s.batched = false;
+    s.launch_mode = kLaunchPerTask;
     s.use_graph = false;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -307,6 +307,7 @@ int build_plan(const wcsp &w, int kind, int i_bound, const int32_t *parent, cons
     if (o.lo_target > 0) P.lo_target = o.lo_target;
     if (o.stage_max_entries > 0) P.stage_max_entries = o.stage_max_entries;
     if (o.stage_max_entries < 0) P.stage_max_entries = 0;
+    P.allow_pipe = o.pipeline >= 0;
 
     // 1. elimination order
     int okind = o.order_kind;

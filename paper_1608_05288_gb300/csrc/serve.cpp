@@ -595,6 +595,7 @@ extern "C" int srv_step(gpube_server *s)
         L.arows_off = static_cast<int32_t>(al(smem, 16));
         L.pipe_off = L.arows_off + (pipe_b ? kMaxPipeRows * 16 : 0);
         if (pipe_b) smem = L.pipe_off + s->threads * pipe_b;
+        smem = place_prefix_smem(L, smem);
         SRV_TRY(cudaMemsetAsync(L.counter, 0, 4, s->stream));
         const int64_t cap = static_cast<int64_t>(util_max_blocks_per_sm(key.first, s->threads, smem)) * s->num_sms;
         const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(tot, cap)));

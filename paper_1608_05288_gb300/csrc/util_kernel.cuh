@@ -1192,6 +1192,37 @@ __device__ __forceinline__ void griddep_launch_dependents()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Dependencies of a launch over several levels: an acquire load of a
+// completion counter, and the wait for every producer task of task a to
+// complete all of its items.  Bounded in time (kWaitNs from the first poll)
+// and in polls; gives up at once when another CTA has set the status word.
+__device__ __forceinline__ int ld_acquire(const int32_t *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool wait_producers(const LaunchDev &L, int a, unsigned long long limit_ns = kWaitNs)
+{
+    const int j0 = L.dep_off[a], j1 = L.dep_off[a + 1];
+    unsigned long long t0 = 0;
+    int polls = 0;
+    for (int j = j0; j < j1; ++j) {
+        const int p = L.deps[j];
+        const int need = L.prefix[p + 1] - L.prefix[p];
+        while (ld_acquire(L.done + p) < need) {
+            if (polls == 0) t0 = global_ns();
+            if (*reinterpret_cast<volatile int32_t *>(L.status) != kStatusOk) return false;
+            if (++polls > kMaxSpin || global_ns() - t0 > limit_ns) return false;
+            __nanosleep(64);
+        }
+    }
+    // the producers' tables may next be read by bulk copies (async proxy)
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    return true;
+}
+
 // ------------------------------------------------------------- kernel
 template <typename C>
 __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
@@ -1200,19 +1231,32 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
     __shared__ uint64_t bar;
     __shared__ int s_item[2];
     __shared__ int s_staged;  // task whose tables are in shared memory, -1 = none
+    __shared__ int s_ready;   // task whose producers are known to be complete, -1 = none
+    __shared__ int s_ok;
 
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&bar, 1);
         s_staged = -1;
+        s_ready = -1;
         s_item[0] = atomicAdd(L.counter, 1);  // this launch's own counter, cleared before the run
         fence_mbar_init();
+    }
+    // the work-item prefixes (written before the launch, like every
+    // descriptor) in shared memory when they fit
+    const int32_t *prefix = L.prefix;
+    if (L.prefix_smem >= 0) {
+        int32_t *sp = reinterpret_cast<int32_t *>(stage + L.prefix_smem);
+        for (int i = tid; i <= L.n_tasks; i += blockDim.x) sp[i] = L.prefix[i];
+        prefix = sp;
     }
     __syncthreads();
     // the next level may be scheduled now: its CTAs become resident only as
     // this launch's CTAs exit (every CTA of this launch is resident already)
     griddep_launch_dependents();
-    // tables written by the previous level are read only after this point
+    // tables written by the previous level are read only after this point.
+    // (The next item is claimed after it too: a CTA that claimed two items
+    // while waiting would take work from the CTAs that start later.)
     griddep_wait();
     uint32_t phase = 0;
     int it = 0;
@@ -1225,12 +1269,27 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
         int a = 0, b = L.n_tasks;
         while (b - a > 1) {
             const int mid = (a + b) >> 1;
-            if (L.prefix[mid] <= item) a = mid;
+            if (prefix[mid] <= item) a = mid;
             else b = mid;
         }
         const TaskDev tk = L.tasks[a];
 
-        const int local = item - L.prefix[a];
+        if (L.done != nullptr && s_ready != a) {
+            // a launch over several levels: wait for the tasks this one reads.
+            // Every thread has read s_ready once all are at this barrier;
+            // only then may thread 0 change it (a thread that read it after
+            // the change would skip the barriers below)
+            __syncthreads();
+            if (tid == 0) {
+                s_ok = wait_producers(L, a) ? 1 : 0;
+                if (!s_ok) atomicExch(L.status, kStatusTimeout);
+                s_ready = a;
+            }
+            __syncthreads();
+            if (!s_ok) return;  // no copy of this CTA is in flight here
+        }
+
+        const int local = item - prefix[a];
         const int hr = local / tk.nlc;
         const int lc = local - hr * tk.nlc;
         const int h0 = hr * tk.hc;
@@ -1273,6 +1332,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
                         lo, h0, h1, L.top_k);
 
         __syncthreads();
+        if (L.done != nullptr && tid == 0) {
+            // every thread's stores of this item precede the barrier above; the
+            // release makes them visible to a CTA whose acquire load sees the count
+            asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(L.done + a) : "memory");
+        }
         item = s_item[nb];
         ++it;
     }

@@ -31,14 +31,14 @@ def _run(st):
     return res
 
 
-@pytest.mark.parametrize("use_graph", [False, True])
+@pytest.mark.parametrize("use_graph,batched", [(False, "level"), (True, "level"), (True, "fused")])
 @pytest.mark.parametrize("kind,mode,z", [("be", "be", 0), ("mbe", "sep", 2)])
-def test_integer_conditioning_sequence(orc, use_graph, kind, mode, z):
+def test_integer_conditioning_sequence(orc, use_graph, batched, kind, mode, z):
     inst = synth.random_small(31, n=10, dmax=3, n_funcs=14, max_arity=3, p_top=0.1)
     ev_vars = [2, 5, 8]
     o, _ = orc.minfill(inst)
     st = gb.UtilState(inst, kind, z, order="given", order_array=o, ibound_mode="sep",
-                      evidence_vars=ev_vars, use_graph=use_graph)
+                      evidence_vars=ev_vars, use_graph=use_graph, batched=batched)
     st.bind()
     cur = {}
     for step in STEPS:

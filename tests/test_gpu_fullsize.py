@@ -12,7 +12,8 @@ import paper_1608_05288_gb300 as gb
 pytestmark = pytest.mark.gpu
 
 
-def test_config1_grid_full_size(orc):
+@pytest.mark.parametrize("batched", ["level", "fused"])
+def test_config1_grid_full_size(orc, batched):
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -20,7 +21,8 @@ def test_config1_grid_full_size(orc):
     import bench
     inst = synth.config_instance(1, 0)
     os.makedirs(os.path.dirname(bench.TUNE_CACHE), exist_ok=True)
-    st = gb.UtilState(inst, "be", order="best", use_graph=True, autotune_cache=bench.TUNE_CACHE)
+    st = gb.UtilState(inst, "be", order="best", use_graph=True, autotune_cache=bench.TUNE_CACHE,
+                      batched=batched)
     st.bind()
     st.autotune()  # the launch shape the benchmark uses
     for _ in range(2):  # the benchmark replays the graph; compare after a replay

@@ -43,7 +43,7 @@ def _case(seed):
                  rows_per_item=int(rng.choice([1, 3, 16, 128])),
                  lo_target=int(rng.choice([1, 5, 64, 2048])),
                  stage_max_entries=int(rng.choice([-1, 4, 0])),
-                 use_graph=bool(rng.random() < 0.5), batched=bool(rng.random() < 0.8))
+                 use_graph=bool(rng.random() < 0.5), batched=int(rng.choice([0, 1, 1, 2, 2])))
     return inst, kind, mode, z, shape
 
 
@@ -73,4 +73,5 @@ def test_random_configuration(orc, seed):
         assert fp_close([res.bound], [run.bound])
         if semiring == "min":  # the GPU's assignment re-evaluated in fp64
             assert fp_close([orc.evaluate(inst, res.assignment)], [res.cost])
-            assert res.cost >= run.bound - 1e-4 * (1 + abs(run.bound))
+            if np.isfinite(run.bound):  # an upper bound of the optimum (MBE) or the optimum
+                assert res.cost >= run.bound - 1e-4 * (1 + abs(run.bound))

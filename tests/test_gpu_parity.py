@@ -32,6 +32,9 @@ LAUNCH_SHAPES = [
     dict(block_threads=32, rows_per_item=1, lo_target=8),  # many tiny items, ragged tails
     dict(block_threads=64, rows_per_item=3, lo_target=5, stage_max_entries=-1),
     dict(block_threads=512, rows_per_item=64, stage_max_entries=4),
+    dict(batched="fused"),                                 # one launch over all levels
+    dict(batched="fused", use_graph=True, block_threads=32, rows_per_item=1, lo_target=8),
+    dict(batched="fused", block_threads=128, rows_per_item=3, lo_target=5, stage_max_entries=4),
 ]
 
 
@@ -162,7 +165,7 @@ def test_config0_grid(orc):
         inst = synth.config_instance(0, seed)
         o, w = orc.minfill(inst)
         run = orc.eliminate(inst, o, "be")
-        for shape in (dict(), dict(batched=False), dict(use_graph=True)):
+        for shape in (dict(), dict(batched=False), dict(use_graph=True), dict(batched="fused")):
             st, res = run_state(inst, "be", **shape)
             check_tables(inst, st, run)
             assert res.bound == run.bound == res.cost
@@ -174,7 +177,7 @@ def test_config2_mbe_full(orc):
     inst = synth.config_instance(2, 0)
     o, _ = orc.minfill(inst)
     run = orc.eliminate(inst, o, "log2", 16)
-    for shape in (dict(use_graph=True), dict(batched=False)):
+    for shape in (dict(use_graph=True), dict(batched=False), dict(batched="fused", use_graph=True)):
         st, res = run_state(inst, "mbe", 16, ibound_mode="log2", **shape)
         check_tables(inst, st, run)
         assert res.bound == run.bound and res.cost == run.cost
@@ -189,12 +192,14 @@ def test_config3_mpe_mbe_and_exact_prefix(orc):
         run = orc.eliminate(inst, o, "sep", 20)
     finally:
         orc.set_threads(1)
-    st, res = run_state(inst, "mbe", 20, ibound_mode="sep", use_graph=True)
-    check_tables(inst, st, run, exact=False)
-    assert fp_close(res.bound, run.bound)
-    # the GPU's own assignment, re-evaluated in fp64 by the oracle
-    assert fp_close(res.cost, orc.evaluate(inst, res.assignment))
-    assert res.bound <= orc.evaluate(inst, res.assignment) + 1e-4 * (1 + abs(res.bound))
+    for shape in (dict(use_graph=True), dict(batched="fused", use_graph=True)):
+        st, res = run_state(inst, "mbe", 20, ibound_mode="sep", **shape)
+        check_tables(inst, st, run, exact=False)
+        assert fp_close(res.bound, run.bound)
+        # the GPU's own assignment, re-evaluated in fp64 by the oracle
+        assert fp_close(res.cost, orc.evaluate(inst, res.assignment))
+        assert res.bound <= orc.evaluate(inst, res.assignment) + 1e-4 * (1 + abs(res.bound))
+        st.free()
     pre = synth.bn_prefix(inst, 60)
     po, _ = orc.minfill(pre)
     prun = orc.eliminate(pre, po, "be")
@@ -263,10 +268,46 @@ def test_autotune_keeps_parity(orc, tmp_path):
     st.bind()
     th, rp = st.autotune()
     assert th in (128, 256, 512) and rp > 0
+    cfg = st.launch_config()
+    assert cfg["block_threads"] == th and cfg["rows_per_item"] == rp
+    assert cfg["lo_target"] in (128, 256, 512, 1024, 2048) and cfg["batched"] in (1, 2)
     st.run()
     res = st.value()
     check_tables(inst, st, run)
     assert res.bound == run.bound
+
+
+def test_autotune_cache_reshapes_bound_state(orc, tmp_path):
+    # configurations read back from the tuning cache are applied to a bound
+    # state: a new lo extent target and staging limit re-shape the tasks in
+    # place (the staged tables change), and the tables stay exact
+    inst = synth.config_instance(2, 1)
+    o, _ = orc.minfill(inst)
+    run = orc.eliminate(inst, o, "log2", 12)
+    first = tmp_path / "first.txt"
+    st = gb.UtilState(inst, "mbe", 12, ibound_mode="log2", use_graph=True, autotune_cache=str(first))
+    st.bind()
+    st.autotune()
+    key = first.read_text().split()[0]
+    st.free()
+    for cfg, staged in (((256, 32, 256, 0, 0, 2), False), ((512, 64, 2048, 4096, 1, 1), True),
+                        ((128, 16, 128, 1024, 1, 2), True)):
+        cache = tmp_path / f"crafted_{cfg[2]}_{cfg[3]}.txt"
+        cache.write_text(key + " " + " ".join(str(x) for x in cfg) + " 1.0\n")
+        st = gb.UtilState(inst, "mbe", 12, ibound_mode="log2", use_graph=True, autotune_cache=str(cache))
+        st.bind()
+        assert any(t["staged_bytes"] for t in st.tasks())  # the default limit stages tables
+        st.autotune()
+        got = st.launch_config()
+        assert (got["block_threads"], got["rows_per_item"], got["lo_target"], int(got["pipeline"]),
+                got["batched"]) == (cfg[0], cfg[1], cfg[2], cfg[4], cfg[5])
+        assert any(t["staged_bytes"] for t in st.tasks()) == staged
+        for _ in range(2):
+            st.run()
+        res = st.value()
+        check_tables(inst, st, run)
+        assert res.bound == run.bound and res.cost == run.cost
+        st.free()
 
 
 @pytest.mark.parametrize("seed", range(8))

@@ -42,6 +42,8 @@ LAUNCH_SHAPES = [
     dict(use_graph=True),
     dict(block_threads=32, rows_per_item=1, lo_target=8),
     dict(block_threads=64, rows_per_item=3, lo_target=5, stage_max_entries=-1),
+    dict(batched="fused", use_graph=True),
+    dict(batched="fused", block_threads=32, rows_per_item=1, lo_target=8),
 ]
 
 
