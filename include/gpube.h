@@ -133,6 +133,11 @@ typedef struct solve_opts {
     int32_t n_evidence_vars;
     int32_t pipeline;          /* 0: group inputs prefetched by the cp.async pipeline where a
                                   task allows it; -1: register variants only              */
+    int32_t vector_rows;       /* 1: a thread computes four consecutive output rows where a
+                                  task allows it (domains 2-3, at most 3 inputs, lo extent
+                                  a multiple of 4): 16-byte cost stores, 4-byte argmin
+                                  stores, block loads of inputs laid out like the output;
+                                  0: one row per thread (default)                          */
 } solve_opts;
 
 /* Result of a solve.  assignment, when non-NULL, is caller-owned host memory
@@ -287,12 +292,14 @@ typedef struct gpube_launch_config {
                                   cp.async pipeline (4-12 groups in flight) where the task
                                   allows it; 0: register variants (1-2 groups in flight)  */
     int32_t launch_mode;       /* solve_opts.batched: 0 per bucket, 1 per level, 2 fused  */
+    int32_t vector_rows;       /* 1: four consecutive rows per thread where a task allows it */
 } gpube_launch_config;
 
 /* Measure candidate launch configurations on this state's own UTIL phase and
  * keep the fastest: CTA size x rows per item, then the lo extent target, the
  * launch mode (per level or one launch over all levels; a per-bucket state
- * keeps its mode), the staging limit and the group-input pipeline, each
+ * keeps its mode), the staging limit, the group-input pipeline and the
+ * four-rows-per-thread variant, each
  * varied around the best so far, then the launch shape once more.  Changing
  * the lo target or the staging limit re-shapes the tasks and rebuilds the
  * offset tables in the bound arena (candidates that do not fit it are

@@ -105,7 +105,7 @@ LAUNCH_MODES = {"bucket": 0, "level": 1, "fused": 2}
 def make_opts(order="minfill", order_array=None, parent=None, ibound_mode="sep", batched=True,
               use_graph=False, block_threads=0, rows_per_item=0, lo_target=0,
               stage_max_entries=0, arena=None, arena_bytes=0, stream=None,
-              autotune_cache=None, device=0, evidence_vars=None, pipeline=True):
+              autotune_cache=None, device=0, evidence_vars=None, pipeline=True, vector_rows=False):
     o = _abi.SolveOpts()
     lib().solve_opts_init(C.byref(o))
     o.order_kind = ORDERS[order] if isinstance(order, str) else int(order)
@@ -138,6 +138,7 @@ def make_opts(order="minfill", order_array=None, parent=None, ibound_mode="sep",
         o.autotune_cache = b
     o.device = int(device)
     o.pipeline = 0 if pipeline else -1
+    o.vector_rows = 1 if vector_rows else 0
     if evidence_vars is not None and len(evidence_vars):
         ev = _i32(evidence_vars)
         keep.append(ev)
@@ -337,7 +338,7 @@ class UtilState:
         _check(lib().util_launch_config(self.h, C.byref(c)))
         return {"block_threads": c.block_threads, "rows_per_item": c.rows_per_item, "lo_target": c.lo_target,
                 "stage_max_entries": c.stage_max_entries if c.stage_max_entries > 0 else -1,
-                "pipeline": bool(c.pipeline), "batched": c.launch_mode}
+                "pipeline": bool(c.pipeline), "batched": c.launch_mode, "vector_rows": bool(c.vector_rows)}
 
     def free(self):
         if getattr(self, "h", None) and _abi._lib is not None:

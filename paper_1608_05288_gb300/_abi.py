@@ -31,12 +31,14 @@ class SolveOpts(C.Structure):
                 ("lo_target", C.c_int32), ("stage_max_entries", C.c_int32),
                 ("arena", C.c_void_p), ("arena_bytes", C.c_size_t), ("stream", C.c_void_p),
                 ("autotune_cache", C.c_char_p), ("device", C.c_int32),
-                ("evidence_vars", i32p), ("n_evidence_vars", C.c_int32), ("pipeline", C.c_int32)]
+                ("evidence_vars", i32p), ("n_evidence_vars", C.c_int32), ("pipeline", C.c_int32),
+                ("vector_rows", C.c_int32)]
 
 
 class LaunchConfig(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("rows_per_item", C.c_int32), ("lo_target", C.c_int32),
-                ("stage_max_entries", C.c_int32), ("pipeline", C.c_int32), ("launch_mode", C.c_int32)]
+                ("stage_max_entries", C.c_int32), ("pipeline", C.c_int32), ("launch_mode", C.c_int32),
+                ("vector_rows", C.c_int32)]
 
 
 class SolveResult(C.Structure):

@@ -566,9 +566,39 @@ int gpube_build_descriptors(util_state *s)
         // rows_per_item counts separator rows; an item spans whole groups
         const int64_t groups = std::max<int64_t>(1, s->cfg.rows_per_item / std::max(T.R0, 1));
         x.hc = static_cast<int32_t>(std::min<int64_t>(groups, T.G));
-        // lo chunks: NT rows (one per thread), or NT / 32 rows for wide
-        // domains (one per warp)
-        const int64_t chunk = dclass_of(T.d) == kDClassWide ? NT / 32 : NT;
+        // four consecutive rows per thread: domains 2..4, at most 3 inputs,
+        // lo extent a multiple of 4, and (single-bucket calls) caller output
+        // tables aligned for the 16-byte and 4-byte stores
+        const bool out_ok = !T.ext_out || (reinterpret_cast<uintptr_t>(T.ext_out) % 16 == 0 &&
+                                           reinterpret_cast<uintptr_t>(T.ext_arg) % 4 == 0);
+        x.v4 = (P.allow_v4 && T.d >= 2 && T.d <= 3 && x.F <= 3 && T.P_lo % 4 == 0 && out_ok) ? 1 : 0;
+        x.lin = 0;
+        x.uni = 0;
+        if (x.v4) {
+            // input f is read in blocks when its strides of the lo digits are d
+            // times the output's (its layout ends with the lo digits and x_i);
+            // it has one offset per aligned block of four rows when it mentions
+            // no lo digit j whose lower digits' product P_j is not a multiple of
+            // 4 (exactly the digits that change inside some aligned block)
+            std::vector<int32_t> st;
+            task_strides(w, P, T, st);
+            const int m = static_cast<int>(T.sep.size());
+            for (int f = 0; f < x.F; ++f) {
+                bool lin = true, uni = true;
+                int64_t pj = 1;
+                for (int j = m - 1; j >= m - T.L; --j) {
+                    const int64_t sf = st[static_cast<size_t>(f) * m + j];
+                    lin = lin && sf == static_cast<int64_t>(T.d) * st[static_cast<size_t>(x.F) * m + j];
+                    if (sf != 0 && pj % 4 != 0) uni = false;
+                    pj *= w.dom[T.sep[j]];
+                }
+                if (lin) x.lin |= 1 << f;
+                else if (uni) x.uni |= 1 << f;
+            }
+        }
+        // lo chunks: NT rows (one per thread), 4 NT rows (four per thread), or
+        // NT / 32 rows for wide domains (one per warp)
+        const int64_t chunk = dclass_of(T.d) == kDClassWide ? NT / 32 : x.v4 ? 4 * NT : NT;
         x.nlc = static_cast<int32_t>((T.P_lo + chunk - 1) / chunk);
         const int64_t items = static_cast<int64_t>(x.nlc) * ((T.G + x.hc - 1) / x.hc);
         if (items > INT32_MAX / 2) return set_error(GPUBE_ENOMEM, "task %d has too many work items", t);
@@ -579,7 +609,7 @@ int gpube_build_descriptors(util_state *s)
         x.n_gi = T.n_gi;
         // one global group input, at most 3 inputs, a fixed-domain variant:
         // prefetch that input with the per-thread cp.async pipeline
-        x.pipe = (P.allow_pipe && x.F <= 3 && T.d >= 2 && T.d <= 8 && T.n_gi - T.n_lo == 1 && T.stage_off[T.n_lo] < 0 &&
+        x.pipe = (!x.v4 && P.allow_pipe && x.F <= 3 && T.d >= 2 && T.d <= 8 && T.n_gi - T.n_lo == 1 && T.stage_off[T.n_lo] < 0 &&
                   T.G > 1)
                      ? 1
                      : 0;
@@ -634,14 +664,14 @@ int gpube_build_descriptors(util_state *s)
         double work = 0.0;  // thread-rows, idle lanes of partial lo chunks included
         for (int i = 0; i < count; ++i) {
             const TaskDev &x = td[first + i];
-            work += static_cast<double>(x.nlc) * NT * x.G * x.R0;
+            work += static_cast<double>(x.nlc) * NT * x.G * x.R0 * (x.v4 ? 4 : 1);
         }
         const double pref = std::max(s->cfg.rows_per_item, 1);
         const double waves = std::max(1.0, std::round(work / (static_cast<double>(cap) * NT * pref)));
         const double rows_per_thread = work / (waves * cap * NT);
         for (int i = 0; i < count; ++i) {
             TaskDev &x = td[first + i];
-            const int64_t hc = std::llround(rows_per_thread / std::max(x.R0, 1));
+            const int64_t hc = std::llround(rows_per_thread / (std::max(x.R0, 1) * (x.v4 ? 4 : 1)));
             x.hc = static_cast<int32_t>(std::min<int64_t>(std::max<int64_t>(hc, 1), x.G));
             if (x.pipe) x.hc = std::min(x.hc, kMaxPipeRows);  // its A rows fit the shared-memory area
             const int64_t items = static_cast<int64_t>(x.nlc) * ((x.G + x.hc - 1) / x.hc);
@@ -1124,18 +1154,18 @@ extern "C" void util_state_free(util_state *s)
 // limit), the group-input pipeline and the launch mode.
 namespace {
 struct TuneCfg {
-    int32_t threads, rows, lo, stage, pipe, mode;
+    int32_t threads, rows, lo, stage, pipe, mode, v4;
     bool operator==(const TuneCfg &o) const
     {
         return threads == o.threads && rows == o.rows && lo == o.lo && stage == o.stage && pipe == o.pipe &&
-               mode == o.mode;
+               mode == o.mode && v4 == o.v4;
     }
 };
 
 TuneCfg current_cfg(const util_state *s)
 {
-    return TuneCfg{s->cfg.threads, s->cfg.rows_per_item, s->plan.lo_target, s->plan.stage_max_entries,
-                   s->plan.allow_pipe ? 1 : 0, s->launch_mode};
+    return TuneCfg{s->cfg.threads,         s->cfg.rows_per_item, s->plan.lo_target, s->plan.stage_max_entries,
+                   s->plan.allow_pipe ? 1 : 0, s->launch_mode,   s->plan.allow_v4 ? 1 : 0};
 }
 
 // Expand the offset tables of a bound state on its stream (after the
@@ -1181,6 +1211,7 @@ static int apply_cfg(util_state *s, const TuneCfg &c)
     s->cfg.threads = c.threads;
     s->cfg.rows_per_item = c.rows;
     P.allow_pipe = c.pipe != 0;
+    P.allow_v4 = c.v4 != 0;
     s->launch_mode = c.mode;
     int rc = upload_descriptors(s);
     if (rc) return rc;
@@ -1211,6 +1242,7 @@ extern "C" int util_launch_config(const util_state *s, gpube_launch_config *out)
     out->stage_max_entries = c.stage;
     out->pipeline = c.pipe;
     out->launch_mode = c.mode;
+    out->vector_rows = c.v4;
     return GPUBE_OK;
 }
 
@@ -1232,7 +1264,7 @@ extern "C" int util_autotune(util_state *s, int32_t *threads, int32_t *rows_per_
             std::string k;
             TuneCfg c{};
             double ms;
-            if (ls >> k >> c.threads >> c.rows >> c.lo >> c.stage >> c.pipe >> c.mode >> ms && k == key) {
+            if (ls >> k >> c.threads >> c.rows >> c.lo >> c.stage >> c.pipe >> c.mode >> c.v4 >> ms && k == key) {
                 int rc = apply_cfg(s, c);
                 if (rc == GPUBE_ENOMEM) break;  // measured with a larger arena: tune here
                 if (rc) return rc;
@@ -1321,6 +1353,11 @@ extern "C" int util_autotune(util_state *s, int32_t *threads, int32_t *rows_per_
             c.pipe = 1 - c.pipe;
             rc = try_all({c});
         }
+        if (!rc) {  // four rows per thread where a task allows it
+            TuneCfg c = best;
+            c.v4 = 1 - c.v4;
+            rc = try_all({c});
+        }
     }
     if (!rc) rc = try_all(shapes());  // the launch shape again, for the chosen decomposition
     if (rc) return rc;
@@ -1329,7 +1366,7 @@ extern "C" int util_autotune(util_state *s, int32_t *threads, int32_t *rows_per_
     if (cache) {
         std::ofstream out(cache, std::ios::app);
         out << key << " " << best.threads << " " << best.rows << " " << best.lo << " " << best.stage << " "
-            << best.pipe << " " << best.mode << " " << best_ms << "\n";
+            << best.pipe << " " << best.mode << " " << best.v4 << " " << best_ms << "\n";
     }
     return report();
 }

@@ -75,7 +75,12 @@ struct alignas(16) TaskDev {
     int32_t nosat;             // integer costs whose row sums stay below the top cost and 2^30
                                // (from upper bounds of the inputs): no saturation, and
                                // (sum << 2 | l) fits in 32 bits
-    int32_t pad0, pad1, pad2;
+    int32_t v4;                // 1: a thread computes four consecutive rows (P_lo % 4 == 0,
+                               // d 2..4, at most 3 inputs); its lo chunk is 4 x blockDim.x rows
+    int32_t lin;               // bit f: input f's layout ends with the lo digits and x_i, so
+                               // B[lo][f] = d * lo (four consecutive rows read one block)
+    int32_t uni;               // bit f: input f has one offset over each aligned block of four
+                               // lo rows (it mentions no digit that varies within one)
 };
 
 // Depth of the per-thread cp.async pipeline of group inputs (groups ahead),

@@ -115,6 +115,7 @@ struct Plan {
     int32_t stage_max_bytes = 32768;
     bool allow_pipe = true;   // group runs prefetched by the per-thread cp.async pipeline (KP groups in
                               // flight) where a task allows it; false: register variants (1-2 groups)
+    bool allow_v4 = false;    // four consecutive rows per thread where a task allows it
     size_t peak_live_bytes = 0;
     ValuePlanH value;
 };

@@ -308,6 +308,7 @@ int build_plan(const wcsp &w, int kind, int i_bound, const int32_t *parent, cons
     if (o.stage_max_entries > 0) P.stage_max_entries = o.stage_max_entries;
     if (o.stage_max_entries < 0) P.stage_max_entries = 0;
     P.allow_pipe = o.pipeline >= 0;
+    P.allow_v4 = o.vector_rows > 0;
 
     // 1. elimination order
     int okind = o.order_kind;

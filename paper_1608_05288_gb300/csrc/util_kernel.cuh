@@ -828,11 +828,127 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     cp_async_wait<0>();
 }
 
+// Four consecutive output rows per thread: rows lo4 .. lo4 + 3 of each hi
+// value (P_lo % 4 == 0, so the four share their hi digits), fixed domain
+// D of 2 or 3, at most 3 inputs.  The four costs go out as one 16-byte store and
+// the four argmins as one 4-byte store.  How an input is read depends on how
+// its offsets vary over the four rows (host-side classes):
+//   bit f of tk.lin: its layout ends with the separator's lo digits and x_i,
+//     so the four rows' runs are one contiguous, 16-byte aligned block of 4D
+//     entries, read with vector loads;
+//   bit f of tk.uni: it mentions none of the digits that vary within an
+//     aligned block of four rows, so one run serves the four rows;
+//   otherwise each row's run is read at its own offset from the B table
+//     (L1-resident), so that no per-row offsets are held in registers.
+// Inputs [0, n_gi) mention no u and are summed once per group, the others
+// once per row.
+template <typename C, int D>
+__device__ __noinline__ void item_v4(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo4, int g0,
+                                     int g1, uint32_t k)
+{
+    const TaskDev tk = *tkp;
+    using T = typename C::val;
+    using A = typename C::acc;
+    constexpr int FC = 3, SA = 4, SB = 4;
+    const int F = tk.F, ngi = tk.n_gi, R0 = tk.R0, lin = tk.lin, uni = tk.uni;
+    const int32_t *Brow = tk.B + static_cast<int64_t>(lo4) * SB;
+    int32_t b0[SB];
+    load_ints<SB>(Brow, b0);
+    const T *ip[FC];
+#pragma unroll
+    for (int f = 0; f < FC; ++f) ip[f] = f < F ? input_base<T>(tk.in[f], stage) + b0[f] : nullptr;
+    int32_t du[SA];
+    load_ints<SA>(tk.A + static_cast<int64_t>(tk.G) * SA, du);
+    T *out = static_cast<T *>(tk.out);
+    uint8_t *arg = tk.arg;
+    // the four rows' runs of input f at hi offset h
+    auto runs = [&](int f, int32_t h, T (&v)[4][D]) {
+        if ((lin >> f) & 1) {
+            T w[4 * D];
+            load_run<4 * D>(ip[f] + h, w);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int l = 0; l < D; ++l) v[i][l] = w[i * D + l];
+        } else if ((uni >> f) & 1) {
+            load_run<D>(ip[f] + h, v[0]);
+#pragma unroll
+            for (int i = 1; i < 4; ++i)
+#pragma unroll
+                for (int l = 0; l < D; ++l) v[i][l] = v[0][l];
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) load_run<D>(ip[f] + (h + (Brow[i * SB + f] - b0[f])), v[i]);
+        }
+    };
+    for (int g = g0; g < g1; ++g) {
+        int32_t a[SA];
+        load_ints<SA>(tk.A + static_cast<int64_t>(g) * SA, a);
+        A pre[4][D];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int l = 0; l < D; ++l) pre[i][l] = A(0);
+#pragma unroll
+        for (int f = 0; f < FC; ++f) {  // lo-only and group inputs (the unrolled loop branches past the rest)
+            if (f >= ngi) break;
+            T v[4][D];
+            runs(f, a[1 + f], v);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int l = 0; l < D; ++l) pre[i][l] = C::add(pre[i][l], v[i][l], k);
+        }
+        int32_t o = a[0] + lo4;
+        int32_t h[FC];
+#pragma unroll
+        for (int f = 0; f < FC; ++f) h[f] = a[1 + f];
+        for (int u = 0; u < R0; ++u) {
+            A acc[4][D];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int l = 0; l < D; ++l) acc[i][l] = pre[i][l];
+#pragma unroll
+            for (int f = 0; f < FC; ++f) {  // per-row inputs
+                if (f >= F) break;
+                if (f < ngi) continue;
+                T v[4][D];
+                runs(f, h[f], v);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int l = 0; l < D; ++l) acc[i][l] = C::add(acc[i][l], v[i][l], k);
+            }
+            T best[4];
+            uint32_t bi = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                int bb;
+                best[i] = C::store(reduce_run<C, D>(acc[i], bb));
+                bi |= static_cast<uint32_t>(bb) << (8 * i);
+            }
+            using V4 = typename std::conditional<std::is_same<T, float>::value, float4, int4>::type;
+            *reinterpret_cast<V4 *>(out + o) = V4{best[0], best[1], best[2], best[3]};
+            if constexpr (!C::kSum) *reinterpret_cast<uint32_t *>(arg + o) = bi;
+            o += du[0];
+#pragma unroll
+            for (int f = 0; f < FC; ++f) h[f] += du[1 + f];
+        }
+    }
+}
+
 template <typename C, int D, int FC>
 __device__ __forceinline__ void item_fixed(const TaskDev *__restrict__ tkp, const TaskDev &tk,
                                            const unsigned char *stage, unsigned char *pipe, const int32_t *arows,
                                            int lo, int g0, int g1, uint32_t k)
 {
+    if constexpr (FC <= 3 && D <= 3) {
+        if (tk.v4) {
+            item_v4<C, D>(tkp, stage, lo, g0, g1, k);
+            return;
+        }
+    }
     if constexpr (FC <= 3) {
         if (tk.pipe) {
             if (tk.R0 <= 4) {
@@ -1324,9 +1440,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
             phase ^= 1u;
         }
 
-        // one thread per row, except the wide variant: one warp per row
+        // one thread per row, except the wide variant (one warp per row) and
+        // the four-row variant (four consecutive rows per thread)
         const bool wide = tk.variant / kNumFClass == kDClassWide;
-        const int lo = wide ? lc * static_cast<int>(blockDim.x >> 5) + (tid >> 5) : lc * blockDim.x + tid;
+        const int lo = wide ? lc * static_cast<int>(blockDim.x >> 5) + (tid >> 5)
+                            : (lc * static_cast<int>(blockDim.x) + tid) * (tk.v4 ? 4 : 1);
         if (lo < tk.P_lo)
             dispatch<C>(L.tasks + a, tk, stage, stage + L.pipe_off, reinterpret_cast<const int32_t *>(stage + L.arows_off),
                         lo, h0, h1, L.top_k);

@@ -43,7 +43,8 @@ def _case(seed):
                  rows_per_item=int(rng.choice([1, 3, 16, 128])),
                  lo_target=int(rng.choice([1, 5, 64, 2048])),
                  stage_max_entries=int(rng.choice([-1, 4, 0])),
-                 use_graph=bool(rng.random() < 0.5), batched=int(rng.choice([0, 1, 1, 2, 2])))
+                 use_graph=bool(rng.random() < 0.5), batched=int(rng.choice([0, 1, 1, 2, 2])),
+                 vector_rows=bool(rng.random() < 0.4))
     return inst, kind, mode, z, shape
 
 

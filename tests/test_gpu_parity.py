@@ -35,6 +35,8 @@ LAUNCH_SHAPES = [
     dict(batched="fused"),                                 # one launch over all levels
     dict(batched="fused", use_graph=True, block_threads=32, rows_per_item=1, lo_target=8),
     dict(batched="fused", block_threads=128, rows_per_item=3, lo_target=5, stage_max_entries=4),
+    dict(vector_rows=True),                                # four consecutive rows per thread
+    dict(vector_rows=True, block_threads=32, rows_per_item=2, lo_target=8, stage_max_entries=-1),
 ]
 
 
@@ -177,7 +179,8 @@ def test_config2_mbe_full(orc):
     inst = synth.config_instance(2, 0)
     o, _ = orc.minfill(inst)
     run = orc.eliminate(inst, o, "log2", 16)
-    for shape in (dict(use_graph=True), dict(batched=False), dict(batched="fused", use_graph=True)):
+    for shape in (dict(use_graph=True), dict(batched=False), dict(batched="fused", use_graph=True),
+                  dict(vector_rows=True, use_graph=True)):
         st, res = run_state(inst, "mbe", 16, ibound_mode="log2", **shape)
         check_tables(inst, st, run)
         assert res.bound == run.bound and res.cost == run.cost
@@ -192,7 +195,7 @@ def test_config3_mpe_mbe_and_exact_prefix(orc):
         run = orc.eliminate(inst, o, "sep", 20)
     finally:
         orc.set_threads(1)
-    for shape in (dict(use_graph=True), dict(batched="fused", use_graph=True)):
+    for shape in (dict(use_graph=True), dict(batched="fused", use_graph=True, vector_rows=True)):
         st, res = run_state(inst, "mbe", 20, ibound_mode="sep", **shape)
         check_tables(inst, st, run, exact=False)
         assert fp_close(res.bound, run.bound)
@@ -290,8 +293,8 @@ def test_autotune_cache_reshapes_bound_state(orc, tmp_path):
     st.autotune()
     key = first.read_text().split()[0]
     st.free()
-    for cfg, staged in (((256, 32, 256, 0, 0, 2), False), ((512, 64, 2048, 4096, 1, 1), True),
-                        ((128, 16, 128, 1024, 1, 2), True)):
+    for cfg, staged in (((256, 32, 256, 0, 0, 2, 1), False), ((512, 64, 2048, 4096, 1, 1, 0), True),
+                        ((128, 16, 128, 1024, 1, 2, 1), True)):
         cache = tmp_path / f"crafted_{cfg[2]}_{cfg[3]}.txt"
         cache.write_text(key + " " + " ".join(str(x) for x in cfg) + " 1.0\n")
         st = gb.UtilState(inst, "mbe", 12, ibound_mode="log2", use_graph=True, autotune_cache=str(cache))
@@ -300,7 +303,7 @@ def test_autotune_cache_reshapes_bound_state(orc, tmp_path):
         st.autotune()
         got = st.launch_config()
         assert (got["block_threads"], got["rows_per_item"], got["lo_target"], int(got["pipeline"]),
-                got["batched"]) == (cfg[0], cfg[1], cfg[2], cfg[4], cfg[5])
+                got["batched"], int(got["vector_rows"])) == (cfg[0], cfg[1], cfg[2], cfg[4], cfg[5], cfg[6])
         assert any(t["staged_bytes"] for t in st.tasks()) == staged
         for _ in range(2):
             st.run()

@@ -44,6 +44,7 @@ LAUNCH_SHAPES = [
     dict(block_threads=64, rows_per_item=3, lo_target=5, stage_max_entries=-1),
     dict(batched="fused", use_graph=True),
     dict(batched="fused", block_threads=32, rows_per_item=1, lo_target=8),
+    dict(vector_rows=True, block_threads=64, lo_target=16),
 ]
 
 
