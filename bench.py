@@ -69,16 +69,20 @@ def whole_job_rate(units_per_rank_step, world, steps, seconds):
     return units_per_rank_step * world * steps / seconds
 
 
-def _traffic_per_launch():
-    """DRAM bytes per UTIL launch from the committed ncu capture, or None when
-    the kernel source changed since that capture."""
+def _traffic_per_launch(alg_bytes_per_launch):
+    """DRAM bytes per UTIL launch of the headline step, from the committed ncu
+    capture of full-size launches of the same grid (traffic taken as
+    proportional to algorithmic bytes), or None when the kernel source changed
+    since that capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         src = os.path.join(ROOT, "paper_1608_05288_gb300", "csrc", "util_kernel.cuh")
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return t["util_kernel_grid12_bytes_per_launch"] if t.get("source_sha256_16") == h else None
+        if t.get("source_sha256_16") != h:
+            return None
+        return t["full_launch_dram_bytes"] / t["full_launch_alg_bytes"] * alg_bytes_per_launch
     except Exception:
         return None
 
@@ -666,7 +670,8 @@ def main():
     peak, peak_kind = _peaks()
     util_s = sum(util_ms) * 1e-3 / args.steps
     achieved = info["alg_bytes"] / util_s / 1e9
-    traffic = _traffic_per_launch()
+    # (the capture behind the traffic figure is of per-level launches)
+    traffic = _traffic_per_launch(info["alg_bytes"] / info["n_levels"]) if tuned["batched"] == 1 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                 "alg_bytes_per_launch": info["alg_bytes"] / (n_launch_step - 1),
