@@ -949,7 +949,7 @@ __device__ __forceinline__ void item_fixed(const TaskDev *__restrict__ tkp, cons
             return;
         }
     }
-    if constexpr (FC <= 3) {
+    if constexpr (FC <= 3 && D <= 8) {  // the host pipelines domains up to 8
         if (tk.pipe) {
             if (tk.R0 <= 4) {
                 switch (tk.F - tk.n_uo) {
@@ -1282,6 +1282,8 @@ __device__ __forceinline__ void dispatch(const TaskDev *__restrict__ tkp, const 
     case 5: dispatch_f<C, 6>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     case 6: dispatch_f<C, 7>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     case 7: dispatch_f<C, 8>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 8: dispatch_f<C, 9>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case 9: dispatch_f<C, 10>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     case kDClassWide:
         if (tk.d <= 128) {
             if (fc == 0) item_wide<C, 3, 4>(tkp, stage, lo, h0, h1, k);
