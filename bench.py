@@ -392,12 +392,16 @@ def serve_bench(torch, gb, synth, n_req):
         wall = time.perf_counter() - t0
         lat = []
         ent = 0
+        alg = 0
         for i in range(n_req):
             ts, ta, td = srv.times(ids[i])
             lat.append(td - ts + lag[i])
-            ent += srv.result(ids[i]).util_entries
+            r = srv.result(ids[i])
+            ent += r.util_entries
+            alg += r.alg_bytes
         st = srv.stats()
         srv.close()
+        st["alg_bytes"] = alg
         return wall, lat, ent, st
 
     # saturated: everything arrives at once
@@ -407,10 +411,24 @@ def serve_bench(torch, gb, synth, n_req):
     arrivals, _ = synth.dcop_stream(n_req, 7, rate)
     wall2, lat2, ent2, st2 = run(arrivals)
     return {"workload": f"{n_req} random DCOPs (20-200 agents, d 5-10, sep <= 8), DPOP UTIL+VALUE",
-            "saturated_instances_per_s": sat, "poisson_rate": rate,
+            "alg_bytes": st2["alg_bytes"], "saturated_instances_per_s": sat, "poisson_rate": rate,
             "instances_per_s": n_req / wall2, "p50_ms": 1e3 * float(np.percentile(lat2, 50)),
             "p99_ms": 1e3 * float(np.percentile(lat2, 99)), "entries_per_s": ent2 / wall2,
             "merged_launches": st2["launches"], "max_inflight": st2["max_inflight"]}
+
+
+def serve_case(args):
+    """The DCOP serving workload alone (GPUBE_SERVE_REQUESTS requests, default
+    300, saturated and then as a Poisson stream at 0.8 x that rate), for
+    launch lists of the merged level launches; prints the serving line."""
+    import torch
+    import synth
+    import paper_1608_05288_gb300 as gb
+    from paper_1608_05288_gb300 import _build
+    _build.build()
+    out = serve_bench(torch, gb, synth, int(os.environ.get("GPUBE_SERVE_REQUESTS", "300")))
+    print(json.dumps({"case": "serve", **out}), flush=True)
+    return 0
 
 
 def bucket_case(args):
@@ -587,7 +605,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--case", default="",
-                    choices=["", "bucket13", "grid3", "grid12", "mrf3", "sweep", "wide100", "er_mbe", "mpe_tasks"])
+                    choices=["", "bucket13", "grid3", "grid12", "mrf3", "sweep", "wide100", "er_mbe", "mpe_tasks",
+                             "serve"])
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0)
     args = ap.parse_args()
@@ -595,6 +614,8 @@ def main():
         return reference_arm(args)
     if args.case == "bucket13":
         return bucket_case(args)
+    if args.case == "serve":
+        return serve_case(args)
     if args.case == "grid3":
         return grid_rows_case(args, 3)
     if args.case == "grid12":
