@@ -645,6 +645,7 @@ int gpube_build_descriptors(util_state *s)
     // shared memory of a launch over tasks [first, first + count): staged
     // tables | the item's A rows | pipeline slots and four per-u partial sums
     // per thread (cp.async path)
+    const int smem_cap = max_dynamic_smem() - 256;  // static shared memory of the kernel
     auto launch_smem = [&](int first, int count, LaunchDev &L) {
         int smem = 0, pipe_b = 0;
         for (int i = 0; i < count; ++i) {
@@ -689,6 +690,9 @@ int gpube_build_descriptors(util_state *s)
         L.prefix = pre_dev + pp;
         L.n_tasks = count;
         const int smem = place_prefix_smem(L, launch_smem(first, count, L));
+        if (smem > smem_cap)
+            return set_error(GPUBE_ENOMEM, "a launch needs %d bytes of shared memory, the device allows %d (lower "
+                             "stage_max_entries or block_threads)", smem, smem_cap);
         const int64_t cap = static_cast<int64_t>(blocks_per_sm(smem)) * s->num_sms;
         int64_t tot = 0;
         int rc = size_items(first, count, cap, &tot, pre + pp);
@@ -714,6 +718,9 @@ int gpube_build_descriptors(util_state *s)
         L.prefix = pre_dev + pp;
         L.n_tasks = static_cast<int32_t>(nt);
         const int smem = place_prefix_smem(L, launch_smem(0, static_cast<int>(nt), L));
+        if (smem > smem_cap)
+            return set_error(GPUBE_ENOMEM, "the launch needs %d bytes of shared memory, the device allows %d "
+                             "(lower stage_max_entries or block_threads)", smem, smem_cap);
         const int64_t cap = static_cast<int64_t>(blocks_per_sm(smem)) * s->num_sms;
         int64_t tot = 0;
         for (int l = 0; l < P.n_levels; ++l) {
@@ -1195,16 +1202,19 @@ static int apply_cfg(util_state *s, const TuneCfg &c)
     Plan &P = s->plan;
     const TuneCfg old = current_cfg(s);
     const bool reshape = c.lo != P.lo_target || c.stage != P.stage_max_entries;
+    const bool was_stale = s->tables_stale;
     if (reshape) {
         P.lo_target = c.lo;
         P.stage_max_entries = c.stage;
         shape_tasks(*s->w, P);
         gpube_layout(s);
+        s->tables_stale = true;
         if (s->arena_bytes > s->arena_cap) {
             P.lo_target = old.lo;
             P.stage_max_entries = old.stage;
             shape_tasks(*s->w, P);
             gpube_layout(s);
+            s->tables_stale = was_stale;  // back to the shape the arena's tables were in before
             return set_error(GPUBE_ENOMEM, "the re-shaped plan does not fit the bound arena");
         }
     }
@@ -1215,10 +1225,15 @@ static int apply_cfg(util_state *s, const TuneCfg &c)
     s->launch_mode = c.mode;
     int rc = upload_descriptors(s);
     if (rc) return rc;
-    if (reshape) {
-        // the status word moved with the layout: it starts at zero again
-        CUDA_TRY(cudaMemsetAsync(s->base + s->status_off, 0, 8, s->stream));
-        return expand_tables(s);
+    // the status word may have moved with a layout (this one's, or that of a
+    // configuration tried before and refused): it starts at zero again
+    CUDA_TRY(cudaMemsetAsync(s->base + s->status_off, 0, 8, s->stream));
+    // after a refused configuration the offset tables may belong to another
+    // shape: expand whenever the shape changed since they were last written
+    if (reshape || s->tables_stale) {
+        rc = expand_tables(s);
+        if (!rc) s->tables_stale = false;
+        return rc;
     }
     return GPUBE_OK;
 }
@@ -1342,7 +1357,7 @@ extern "C" int util_autotune(util_state *s, int32_t *threads, int32_t *rows_per_
     }
     if (!rc) {  // staging limit (0: no table staged) and the group-input pipeline
         std::vector<TuneCfg> v;
-        for (int st : {0, 1024, 4096}) {
+        for (int st : {0, 1024, 4096, 32768}) {
             TuneCfg c = best;
             c.stage = st;
             v.push_back(c);

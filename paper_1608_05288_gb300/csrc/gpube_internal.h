@@ -157,6 +157,7 @@ cudaError_t launch_expand(const ExpandDev *tasks, const int64_t *prefix, int n_t
 cudaError_t launch_value(const ValueDev &V, int ktype, int smem, cudaStream_t s);
 cudaError_t launch_value_batch(const ValueBatch &B, int ktype, int smem, cudaStream_t s);
 cudaError_t kernels_init_device();
+int max_dynamic_smem();
 cudaError_t launch_selftest_wait(int32_t *status, unsigned long long limit_ns, cudaStream_t s);
 
 }  // namespace gpube
@@ -197,6 +198,7 @@ struct util_state {
     size_t work_off = 0;         // counters + status + result
     size_t arena_bytes = 0;
     size_t arena_cap = 0;         // bytes of the bound arena (a re-shaped plan must fit in it)
+    bool tables_stale = false;    // re-shaped since the offset tables were last expanded
     // device binding
     int device = 0;
     unsigned char *base = nullptr;

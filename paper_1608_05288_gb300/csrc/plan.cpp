@@ -520,6 +520,11 @@ void task_strides(const wcsp &w, const Plan &P, const Task &T, std::vector<int32
 // they are read, and choose the staged inputs.
 void shape_tasks(const wcsp &w, Plan &P)
 {
+    // staged bytes per task: the byte limit, or room for one table at the
+    // entry limit when that is larger (up to 160 KB, which leaves shared
+    // memory for the pipeline slots of a 128-thread CTA)
+    const int64_t stage_cap = std::min<int64_t>(std::max<int64_t>(P.stage_max_bytes, 4LL * P.stage_max_entries),
+                                                160 * 1024);
     // scratch lists reused across tasks (cleared per task)
     std::vector<int32_t> absent, present, lo_only, group, u_only, row;
     std::vector<int> idx;
@@ -588,7 +593,7 @@ void shape_tasks(const wcsp &w, Plan &P)
             if (sz > P.stage_max_entries) break;
             if (fn.ext && (sz * 4) % kStageAlign) continue;  // a copy would read past the caller's table
             const int64_t bytes = static_cast<int64_t>(align_up(sz * 4, kStageAlign));
-            if (T.stage_bytes + bytes > P.stage_max_bytes) break;
+            if (T.stage_bytes + bytes > stage_cap) break;
             T.stage_off[f] = T.stage_bytes;
             T.stage_bytes += static_cast<int32_t>(bytes);
         }

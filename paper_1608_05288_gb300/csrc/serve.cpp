@@ -372,6 +372,9 @@ extern "C" int64_t srv_submit(gpube_server *s, wcsp *w, int32_t kind, int32_t i_
     // small requests: inner row blocks of two CTAs' width keep the per-task
     // offset tables (one row per inner row) small
     if (o.lo_target <= 0) o.lo_target = 2 * s->threads;
+    // merged launches take the largest shared-memory need of their tasks:
+    // keep staged tables at the default limit
+    if (o.stage_max_entries == 0 || o.stage_max_entries > 4096) o.stage_max_entries = 4096;
     // copies of everything the plan reads, owned by the request
     const int n = w->n;
     wcsp_ref(w);

@@ -183,6 +183,19 @@ cudaError_t launch_value_batch(const ValueBatch &B, int ktype, int smem, cudaStr
     return ktype == kKTypeInt ? launch_value_batch_i32(B, smem, s) : launch_value_batch_f32(B, smem, s);
 }
 
+// Largest dynamic shared memory a UTIL launch may request on the current
+// device (the attribute kernels_init_device sets).
+int max_dynamic_smem()
+{
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 48 * 1024;
+    }
+    return optin - 1024;
+}
+
 // Once per device (current device): allow every kernel the device's largest
 // dynamic shared-memory size, so that no launch needs an attribute change
 // (in particular none during a stream capture).
