@@ -431,6 +431,54 @@ def serve_case(args):
     return 0
 
 
+def mpe_bucket_case(args):
+    """One mini-bucket of the MPE bound (Bayesian network n=200, MBE i=20) on
+    its own through util_bucket: the same separator and input scopes as task
+    --task of the plan, fp32 tables of random -log p values, the plan's
+    default decomposition.  Times --steps launches (median) for kernel
+    profiles of that bucket shape."""
+    import torch
+    import synth
+    import paper_1608_05288_gb300 as gb
+    from paper_1608_05288_gb300 import _build
+    _build.build()
+    inst = synth.config_instance(3, 0)
+    st = gb.UtilState(inst, "mbe", 20, ibound_mode="sep")
+    tasks = st.tasks()
+    T = tasks[args.task]
+    sep = [int(v) for v in T["sep"]]
+    d = int(inst.dom[T["var"]])
+    nf = inst.n_funcs
+    g = torch.Generator(device="cuda").manual_seed(args.task)
+    tabs, positions = [], []
+    alg = 5 * int(T["rows"])
+    for fid in (int(x) for x in T["inputs"]):
+        scope = [int(v) for v in (inst.scopes[fid] if fid < nf else tasks[fid - nf]["sep"])]
+        pos = sorted(sep.index(v) for v in scope if v != T["var"])
+        size = int(np.prod([int(inst.dom[sep[p]]) for p in pos])) * d if pos else d
+        tabs.append(torch.rand(size, generator=g, device="cuda") * 5.0)
+        positions.append(pos)
+        alg += 4 * size
+    sep_dom = [int(inst.dom[v]) for v in sep]
+    out = torch.empty(int(T["rows"]), dtype=torch.float32, device="cuda")
+    arg = torch.empty(int(T["rows"]), dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        gb.util_bucket(sep_dom, d, tabs, positions, out, arg, "real")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        ev[k][0].record()
+        gb.util_bucket(sep_dom, d, tabs, positions, out, arg, "real")
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    peak, kind = _peaks()
+    print(json.dumps({"case": "mpe_bucket", "task": args.task, "d": d, "rows": int(T["rows"]),
+                      "inputs": [len(t) for t in tabs], "ms": ms, "alg_bytes": alg,
+                      "gbs": alg / ms / 1e6, "frac": alg / ms / 1e6 / peak}), flush=True)
+    return 0
+
+
 def bucket_case(args):
     """The grid's largest bucket alone through util_bucket: separator of 12
     variables (d = 4), inputs = the previous bucket function (the 12 lowest
@@ -606,7 +654,8 @@ def main():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--case", default="",
                     choices=["", "bucket13", "grid3", "grid12", "mrf3", "sweep", "wide100", "er_mbe", "mpe_tasks",
-                             "serve"])
+                             "serve", "mpe_bucket"])
+    ap.add_argument("--task", type=int, default=165)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0)
     args = ap.parse_args()
@@ -616,6 +665,8 @@ def main():
         return bucket_case(args)
     if args.case == "serve":
         return serve_case(args)
+    if args.case == "mpe_bucket":
+        return mpe_bucket_case(args)
     if args.case == "grid3":
         return grid_rows_case(args, 3)
     if args.case == "grid12":

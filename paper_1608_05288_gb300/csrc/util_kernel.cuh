@@ -463,13 +463,12 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
 #pragma unroll
             for (int j = 0; j < NG; ++j) {
                 oo[j] = a[j][0] + lo;
+                // the per-row inputs' offsets of the group, read at their column
+                // of the A row (already in L1) rather than selected out of the
+                // registers by the runtime input index
+                const int32_t *ar = tk.A + static_cast<int64_t>(g + j < g1 ? g + j : g) * SA + 1 + ngi;
 #pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    ro[j][r] = 0;
-#pragma unroll
-                    for (int f = 0; f < FC; ++f)
-                        if (f == ngi + r) ro[j][r] = a[j][1 + f];
-                }
+                for (int r = 0; r < NR; ++r) ro[j][r] = ar[r];
             }
         }
         const int nj = (g + 1 < g1) ? NG : 1;
@@ -725,12 +724,8 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
         slot_load<D, CH>(pipe_s + static_cast<uint32_t>(slot * NCH * NT * CH), NT, tid, x);
         int32_t ro[R];
 #pragma unroll
-        for (int r = 0; r < NRG; ++r) {
-            ro[r] = 0;
-#pragma unroll
-            for (int f = 0; f < FC; ++f)
-                if (f == rg0 + r) ro[r] = a[1 + f];
-        }
+        for (int r = 0; r < NRG; ++r)  // the per-row inputs' offsets, at their column of the A row
+            ro[r] = lds_int(arows_s + static_cast<uint32_t>(((g - g0) * SA + 1 + rg0 + r) * 4));
         int32_t o = a[0] + lo;
         if constexpr (SF) {
             float mx = x[0];
