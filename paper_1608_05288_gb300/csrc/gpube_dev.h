@@ -24,14 +24,18 @@ constexpr int kKTypeSum = 2;
 
 // Kernel variants: the eliminated domain class times the input-count class.
 // D class 0 = any domain size (runtime loop, one thread per row); 1..9 =
-// domain 2..10; 10 = wide domains (>= 32 values: a warp per row, lanes over
-// the values, warp-shuffle min / argmin).
+// domain 2..10; 10 = domain 16; 11 = wide domains (>= 32 values: a warp per
+// row, lanes over the values, warp-shuffle min / argmin).
 // F class 0..2 = at most 3 or 7 inputs held in registers (A rows of 4 or 8
 // ints, B rows of 4 or 8 ints); 2 = any count.
 constexpr int kNumFClass = 3;
 constexpr int kWideD = 32;
-constexpr int kDClassWide = 10;
-inline int dclass_of(int d) { return (d >= 2 && d <= 10) ? d - 1 : d >= kWideD ? kDClassWide : 0; }
+constexpr int kDClass16 = 10;
+constexpr int kDClassWide = 11;
+inline int dclass_of(int d)
+{
+    return (d >= 2 && d <= 10) ? d - 1 : d == 16 ? kDClass16 : d >= kWideD ? kDClassWide : 0;
+}
 inline int fclass_of(int F) { return F <= 3 ? 0 : F <= 7 ? 1 : 2; }
 // Row widths of the A (output + inputs) and B (inputs) offset tables.
 inline int arow_of(int F) { return F <= 3 ? 4 : F <= 7 ? 8 : (F + 1 + 3) / 4 * 4; }

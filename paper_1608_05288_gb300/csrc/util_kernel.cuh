@@ -385,6 +385,82 @@ __device__ __noinline__ void item_fixed_anyF(const TaskDev *__restrict__ tkp, co
     }
 }
 
+// Fixed domain D, more than 7 inputs, at most 8 of them group inputs and at
+// most 2 per-row inputs (the shape of the hub buckets of scale-free graphs:
+// many small tables on the hub and the separator): the base pointers of the
+// group and per-row inputs, their row lo included, stay in registers for the
+// whole item, so a group costs one A-row entry and one run per group input and
+// a row one run per per-row input, with no descriptor loads.
+template <typename C, int D>
+__device__ __noinline__ void item_fixed_manyF(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo,
+                                              int g0, int g1, uint32_t k)
+{
+    const TaskDev tk = *tkp;
+    using T = typename C::val;
+    using A = typename C::acc;
+    constexpr int GMAX = 8, RMAX = 2;
+    const int F = tk.F, nlo = tk.n_lo, ngi = tk.n_gi, ng = ngi - nlo, nr = F - ngi;
+    const int32_t *Brow = tk.B + static_cast<int64_t>(lo) * tk.sb;
+    const int32_t *du = tk.A + static_cast<int64_t>(tk.G) * tk.sa;
+    T *out = static_cast<T *>(tk.out);
+    A base[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) base[l] = A(0);
+    for (int f = 0; f < nlo; ++f) {
+        T v[D];
+        load_run<D>(input_base<T>(tk.in[f], stage) + Brow[f], v);
+#pragma unroll
+        for (int l = 0; l < D; ++l) base[l] = C::add(base[l], v[l], k);
+    }
+    const T *gp[GMAX];
+#pragma unroll
+    for (int i = 0; i < GMAX; ++i) gp[i] = i < ng ? input_base<T>(tk.in[nlo + i], stage) + Brow[nlo + i] : nullptr;
+    const T *rp[RMAX];
+    int32_t dr[RMAX];
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+        rp[r] = r < nr ? input_base<T>(tk.in[ngi + r], stage) + Brow[ngi + r] : nullptr;
+        dr[r] = r < nr ? du[1 + ngi + r] : 0;
+    }
+    for (int g = g0; g < g1; ++g) {
+        const int32_t *Ar = tk.A + static_cast<int64_t>(g) * tk.sa;
+        A pre[D];
+#pragma unroll
+        for (int l = 0; l < D; ++l) pre[l] = base[l];
+#pragma unroll
+        for (int i = 0; i < GMAX; ++i) {
+            if (i >= ng) break;
+            T v[D];
+            load_run<D>(gp[i] + Ar[1 + nlo + i], v);
+#pragma unroll
+            for (int l = 0; l < D; ++l) pre[l] = C::add(pre[l], v[l], k);
+        }
+        int32_t o = Ar[0] + lo;
+        int32_t ro[RMAX];
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) ro[r] = r < nr ? Ar[1 + ngi + r] : 0;
+        for (int u = 0; u < tk.R0; ++u) {
+            A acc[D];
+#pragma unroll
+            for (int l = 0; l < D; ++l) acc[l] = pre[l];
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r) {
+                if (r >= nr) break;
+                T v[D];
+                load_run<D>(rp[r] + ro[r], v);
+                ro[r] += dr[r];
+#pragma unroll
+                for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
+            }
+            int bi;
+            const A best = reduce_run<C, D>(acc, bi);
+            out[o] = C::store(best);
+            if constexpr (!C::kSum) tk.arg[o] = static_cast<uint8_t>(bi);
+            o += du[0];
+        }
+    }
+}
+
 // One item for a fixed domain D, at most FC inputs (FC = 3 or 7: A rows of
 // FC + 1 ints, one or two 16-byte loads) of which NR are per-row inputs
 // (they mention the fastest hi digit u).  Lo-only inputs are summed once per
@@ -1258,7 +1334,15 @@ __device__ __forceinline__ void dispatch_f(const TaskDev *__restrict__ tkp, cons
         switch (fc) {
         case 0: item_fixed<C, D, 3>(tkp, tk, stage, pipe, arows, lo, h0, h1, k); break;
         case 1: item_fixed<C, D, 7>(tkp, tk, stage, pipe, arows, lo, h0, h1, k); break;
-        default: item_fixed_anyF<C, D>(tkp, stage, lo, h0, h1, k); break;
+        default:
+            if constexpr (D <= 10) {
+                if (tk.n_gi - tk.n_lo <= 8 && tk.F - tk.n_gi <= 2) {
+                    item_fixed_manyF<C, D>(tkp, stage, lo, h0, h1, k);
+                    break;
+                }
+            }
+            item_fixed_anyF<C, D>(tkp, stage, lo, h0, h1, k);
+            break;
         }
     }
 }
@@ -1279,6 +1363,7 @@ __device__ __forceinline__ void dispatch(const TaskDev *__restrict__ tkp, const 
     case 7: dispatch_f<C, 8>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     case 8: dispatch_f<C, 9>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     case 9: dispatch_f<C, 10>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
+    case kDClass16: dispatch_f<C, 16>(tkp, tk, fc, stage, pipe, arows, lo, h0, h1, k); break;
     case kDClassWide:
         if (tk.d <= 128) {
             if (fc == 0) item_wide<C, 3, 4>(tkp, stage, lo, h0, h1, k);

@@ -84,7 +84,7 @@ def test_random_be_all_launch_shapes(orc, seed, shape):
     assert res.cost == run.cost and list(res.assignment) == list(run.sigma)
 
 
-@pytest.mark.parametrize("dom", [(1, 3), (2, 2), (3, 3), (5, 5), (7, 8), (9, 12), (2, 8)])
+@pytest.mark.parametrize("dom", [(1, 3), (2, 2), (3, 3), (5, 5), (7, 8), (9, 10), (9, 12), (16, 16), (2, 8)])
 def test_domain_classes(orc, dom):
     # every templated domain size (2..8), the generic loop (1, 9..12)
     inst = synth.random_small(17 + dom[0], n=7, dmin=dom[0], dmax=dom[1], n_funcs=10, max_arity=3)
@@ -93,6 +93,37 @@ def test_domain_classes(orc, dom):
     st, res = run_state(inst, "be", order="given", order_array=o, block_threads=64, lo_target=16)
     check_tables(inst, st, run)
     assert res.bound == run.bound and list(res.assignment) == list(run.sigma)
+
+
+@pytest.mark.parametrize("cost_type", ["int", "real"])
+@pytest.mark.parametrize("d", [2, 3, 5])
+def test_hub_bucket_many_inputs(orc, cost_type, d):
+    # a hub with ten binary tables to leaves that form a chain, the hub
+    # eliminated first: its bucket has ten inputs, three on the lo digits,
+    # six group inputs and one on the fastest hi digit (the many-input
+    # variant that keeps their pointers in registers)
+    rng = np.random.default_rng(d)
+    n = 11
+    dom = np.full(n, d, dtype=np.int32)
+    scopes = [np.array([0, v], np.int32) for v in range(1, n)] + [np.array([v, v + 1], np.int32) for v in range(1, n - 1)]
+    tables = []
+    for sc in scopes:
+        size = d * d
+        tables.append(rng.integers(0, 500, size=size).astype(np.int64) if cost_type == "int"
+                      else -np.log(rng.uniform(0.01, 1.0, size=size)))
+    inst = synth.Instance("hub", dom, scopes, tables, cost_type, 1 << 30)
+    order = np.arange(n)
+    for shape in (dict(lo_target=d * d * d, block_threads=32, rows_per_item=4), dict(lo_target=d * d, batched="fused")):
+        st, res = run_state(inst, "be", order="given", order_array=order, **shape)
+        t0 = st.task(0)
+        assert len(t0["inputs"]) == 10 and t0["n_group"] - t0["n_lo"] <= 8 and 10 - t0["n_group"] <= 2
+        run = orc.eliminate(inst, order, "be")
+        check_tables(inst, st, run, exact=(cost_type == "int"))
+        if cost_type == "int":
+            assert res.bound == run.bound and list(res.assignment) == list(run.sigma)
+        else:
+            assert fp_close(res.bound, run.bound)
+        st.free()
 
 
 @pytest.mark.parametrize("nf", [5, 9, 20])
