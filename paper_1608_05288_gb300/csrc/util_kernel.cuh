@@ -67,6 +67,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+// Raise an mbarrier phase's expected transaction bytes without arriving.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
     asm volatile(
@@ -1452,6 +1459,32 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
     // the next level may be scheduled now: its CTAs become resident only as
     // this launch's CTAs exit (every CTA of this launch is resident already)
     griddep_launch_dependents();
+    // the first item's offset rows (cp.async path) are descriptors written
+    // before the launch: thread 0 starts their copy while the previous level
+    // completes (the bytes are expected on the barrier without an arrival; the
+    // item's own arrival below completes the phase)
+    bool early = false;
+    if (s_item[0] < L.total_items) {
+        const int item0 = s_item[0];
+        int a = 0, b = L.n_tasks;
+        while (b - a > 1) {
+            const int mid = (a + b) >> 1;
+            if (prefix[mid] <= item0) a = mid;
+            else b = mid;
+        }
+        const TaskDev *t0 = L.tasks + a;
+        if (t0->pipe) {
+            if (tid == 0) {
+                const int nlc = t0->nlc, hc = t0->hc, G = t0->G;
+                const int h0 = ((item0 - prefix[a]) / nlc) * hc;
+                const uint32_t rows_bytes = static_cast<uint32_t>(min(h0 + hc, G) - h0) * 16u;
+                fence_proxy_async();
+                mbar_expect_tx(&bar, rows_bytes);
+                tma_bulk_g2s(stage + L.arows_off, t0->A + static_cast<int64_t>(h0) * 4, rows_bytes, &bar);
+            }
+            early = true;
+        }
+    }
     // tables written by the previous level are read only after this point.
     // (The next item is claimed after it too: a CTA that claimed two items
     // while waiting would take work from the CTAs that start later.)
@@ -1484,7 +1517,13 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
                 s_ready = a;
             }
             __syncthreads();
-            if (!s_ok) return;  // no copy of this CTA is in flight here
+            if (!s_ok) {
+                if (early) {  // let the first item's offset rows land (bounded) before leaving
+                    if (tid == 0) mbar_arrive_expect_tx(&bar, 0u);
+                    mbar_wait_bounded(&bar, phase);
+                }
+                return;
+            }
         }
 
         const int local = item - prefix[a];
@@ -1496,8 +1535,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
         // has not staged them yet) and, for the cp.async path, the item's
         // contiguous A rows
         const bool restage = tk.stage_bytes > 0 && s_staged != a;
-        const uint32_t rows_bytes = tk.pipe ? static_cast<uint32_t>(h1 - h0) * 16u : 0u;
-        if (restage || rows_bytes) {
+        const uint32_t rows_bytes = (tk.pipe && !early) ? static_cast<uint32_t>(h1 - h0) * 16u : 0u;
+        if (restage || rows_bytes || early) {
             __syncthreads();  // every thread is done with the previous copies
             if (tid == 0) {
                 fence_proxy_async();
@@ -1538,6 +1577,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
             asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(L.done + a) : "memory");
         }
         item = s_item[nb];
+        early = false;
         ++it;
     }
 }
