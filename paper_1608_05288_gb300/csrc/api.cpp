@@ -605,6 +605,9 @@ int gpube_build_descriptors(util_state *s)
         x.n_items = static_cast<int32_t>(items);
         x.variant = dclass_of(T.d) * kNumFClass + fclass_of(x.F);
         x.stage_bytes = T.stage_bytes;
+        x.cin = 1;
+        for (size_t f = 0; f < T.inputs.size(); ++f)
+            if (T.stage_off[f] >= 0 && P.funcs[T.inputs[f]].task >= 0) x.cin = 0;
         x.n_lo = T.n_lo;
         x.n_gi = T.n_gi;
         // one global group input, at most 3 inputs, a fixed-domain variant:

@@ -85,7 +85,12 @@ struct alignas(16) TaskDev {
                                // B[lo][f] = d * lo (four consecutive rows read one block)
     int32_t uni;               // bit f: input f has one offset over each aligned block of four
                                // lo rows (it mentions no digit that varies within one)
+    int32_t cin;               // 1: every staged input is a table the run does not write (an
+                               // original), so it may be copied before the previous launch ends
+    int32_t pad3;
 };
+
+static_assert(sizeof(TaskDev) == 128, "a task descriptor is one 128-byte line");
 
 // Depth of the per-thread cp.async pipeline of group inputs (groups ahead),
 // and the most groups one item of that path spans (its A rows are copied to

@@ -1460,9 +1460,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
     // this launch's CTAs exit (every CTA of this launch is resident already)
     griddep_launch_dependents();
     // the first item's offset rows (cp.async path) are descriptors written
-    // before the launch: thread 0 starts their copy while the previous level
-    // completes (the bytes are expected on the barrier without an arrival; the
-    // item's own arrival below completes the phase)
+    // before the launch, and its staged tables may all be originals, which
+    // the run does not write: thread 0 starts those copies while the previous
+    // level completes (the bytes are expected on the barrier without an
+    // arrival; the item's own arrival below completes the phase)
     bool early = false;
     if (s_item[0] < L.total_items) {
         const int item0 = s_item[0];
@@ -1473,18 +1474,29 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
             else b = mid;
         }
         const TaskDev *t0 = L.tasks + a;
-        if (t0->pipe) {
+        const bool rows = t0->pipe != 0;
+        const bool stg = t0->stage_bytes > 0 && t0->cin;
+        if (rows || stg) {
             if (tid == 0) {
                 const int nlc = t0->nlc, hc = t0->hc, G = t0->G;
                 const int h0 = ((item0 - prefix[a]) / nlc) * hc;
-                const uint32_t rows_bytes = static_cast<uint32_t>(min(h0 + hc, G) - h0) * 16u;
+                const uint32_t rows_bytes = rows ? static_cast<uint32_t>(min(h0 + hc, G) - h0) * 16u : 0u;
                 fence_proxy_async();
-                mbar_expect_tx(&bar, rows_bytes);
-                tma_bulk_g2s(stage + L.arows_off, t0->A + static_cast<int64_t>(h0) * 4, rows_bytes, &bar);
+                mbar_expect_tx(&bar, rows_bytes + (stg ? static_cast<uint32_t>(t0->stage_bytes) : 0u));
+                if (stg) {
+                    for (int f = 0; f < t0->F; ++f) {
+                        const InDev in = t0->in[f];
+                        if (in.stage_off >= 0)
+                            tma_bulk_g2s(stage + in.stage_off, in.ptr, static_cast<uint32_t>(in.bytes16), &bar);
+                    }
+                    s_staged = a;
+                }
+                if (rows) tma_bulk_g2s(stage + L.arows_off, t0->A + static_cast<int64_t>(h0) * 4, rows_bytes, &bar);
             }
             early = true;
         }
     }
+    __syncthreads();  // s_staged
     // tables written by the previous level are read only after this point.
     // (The next item is claimed after it too: a CTA that claimed two items
     // while waiting would take work from the CTAs that start later.)
@@ -1518,7 +1530,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
             }
             __syncthreads();
             if (!s_ok) {
-                if (early) {  // let the first item's offset rows land (bounded) before leaving
+                if (early) {  // let the first item's early copies land (bounded) before leaving
                     if (tid == 0) mbar_arrive_expect_tx(&bar, 0u);
                     mbar_wait_bounded(&bar, phase);
                 }
