@@ -1291,24 +1291,34 @@ extern "C" int util_autotune(util_state *s, int32_t *threads, int32_t *rows_per_
         }
     }
     // time one configuration: the mean of two runs after one warm-up run
-    auto measure = [&](const TuneCfg &c, double *ms) {
+    // time one configuration: the median of n runs after one warm-up run, n
+    // enough for about 4 ms of timed runs (2 to 15; short runs are noisier),
+    // times the given factor
+    auto measure = [&](const TuneCfg &c, double *ms, int factor) {
         int rc = apply_cfg(s, c);
         if (rc) return rc;
-        double tot = 0.0;
-        for (int rep = 0; rep < 3; ++rep) {
+        std::vector<double> t;
+        int n = 2;
+        for (int rep = 0; rep <= n; ++rep) {
             rc = util_run(s);
             if (!rc) rc = util_sync(s);
             if (rc) return rc;
-            double t;
-            util_last_times(s, &t, nullptr);
-            if (rep > 0) tot += t;
+            double x;
+            util_last_times(s, &x, nullptr);
+            if (rep == 0) {
+                n = factor * std::max(2, std::min(15, static_cast<int>(4.0 / std::max(x, 1e-3))));
+                continue;
+            }
+            t.push_back(x);
         }
-        *ms = tot / 2;
+        std::nth_element(t.begin(), t.begin() + t.size() / 2, t.end());
+        *ms = t[t.size() / 2];
         return GPUBE_OK;
     };
     TuneCfg best = current_cfg(s);
     double best_ms = 1e30;
     std::vector<TuneCfg> seen;
+    std::vector<std::pair<double, int>> timed;  // (ms, index into seen) of every configuration run
     // coordinate descent: each stage varies one part of the configuration
     // around the best one so far (a candidate already timed is skipped)
     auto try_all = [&](const std::vector<TuneCfg> &cands) {
@@ -1316,9 +1326,10 @@ extern "C" int util_autotune(util_state *s, int32_t *threads, int32_t *rows_per_
             if (std::find(seen.begin(), seen.end(), c) != seen.end()) continue;
             seen.push_back(c);
             double ms;
-            int rc = measure(c, &ms);
+            int rc = measure(c, &ms, 1);
             if (rc == GPUBE_ENOMEM) continue;  // does not fit the bound arena
             if (rc) return rc;
+            timed.push_back({ms, static_cast<int>(seen.size()) - 1});
             if (ms < best_ms) {
                 best_ms = ms;
                 best = c;
@@ -1339,46 +1350,67 @@ extern "C" int util_autotune(util_state *s, int32_t *threads, int32_t *rows_per_
             }
         return v;
     };
-    int rc = try_all(shapes());
-    if (!rc) {  // lo extent target of the work decomposition
+    // lo extent target of the work decomposition
+    auto los = [&]() {
         std::vector<TuneCfg> v;
         for (int lo : {128, 256, 512, 1024, 2048}) {
             TuneCfg c = best;
             c.lo = lo;
             v.push_back(c);
         }
-        rc = try_all(v);
-    }
-    if (!rc && s->plan.n_levels > 1) {  // one launch per level, or one over all levels
-        std::vector<TuneCfg> v;
-        for (int mode : {kLaunchPerLevel, kLaunchFused}) {
-            TuneCfg c = best;
-            c.mode = mode;
-            v.push_back(c);
+        return v;
+    };
+    int rc = try_all(shapes());
+    if (!rc) rc = try_all(los());
+    // two passes over the other dimensions, each around the best so far (one
+    // pass can stop in a corner: a staging limit that only pays with the
+    // pipeline on, kept after the pipeline is switched off)
+    for (int pass = 0; pass < 2 && !rc; ++pass) {
+        if (s->plan.n_levels > 1 && s->launch_mode != kLaunchPerTask) {
+            // one launch per level, or one over all levels, each with every lo
+            // target (the best target differs between the two forms)
+            std::vector<TuneCfg> v;
+            for (int mode : {kLaunchPerLevel, kLaunchFused})
+                for (int lo : {128, 256, 512, 1024, 2048}) {
+                    TuneCfg c = best;
+                    c.mode = mode;
+                    c.lo = lo;
+                    v.push_back(c);
+                }
+            rc = try_all(v);
         }
-        if (s->launch_mode != kLaunchPerTask) rc = try_all(v);
-    }
-    if (!rc) {  // staging limit (0: no table staged) and the group-input pipeline
-        std::vector<TuneCfg> v;
-        for (int st : {0, 1024, 4096, 32768}) {
-            TuneCfg c = best;
-            c.stage = st;
-            v.push_back(c);
-        }
-        rc = try_all(v);
-        if (!rc) {
-            TuneCfg c = best;
-            c.pipe = 1 - c.pipe;
-            rc = try_all({c});
+        if (!rc) {  // staging limit (0: no table staged) and the group-input pipeline
+            std::vector<TuneCfg> v;
+            for (int st : {0, 1024, 4096, 32768})
+                for (int pipe : {0, 1}) {
+                    TuneCfg c = best;
+                    c.stage = st;
+                    c.pipe = pipe;
+                    v.push_back(c);
+                }
+            rc = try_all(v);
         }
         if (!rc) {  // four rows per thread where a task allows it
             TuneCfg c = best;
             c.v4 = 1 - c.v4;
             rc = try_all({c});
         }
+        if (!rc) rc = try_all(shapes());  // the launch shape again, for the chosen decomposition
+        if (!rc) rc = try_all(los());       // and the lo target for that shape
     }
-    if (!rc) rc = try_all(shapes());  // the launch shape again, for the chosen decomposition
     if (rc) return rc;
+    // the three fastest configurations timed again with three times the runs
+    std::sort(timed.begin(), timed.end());
+    best_ms = 1e30;
+    for (size_t i = 0; i < timed.size() && i < 3; ++i) {
+        double ms;
+        rc = measure(seen[timed[i].second], &ms, 3);
+        if (rc) return rc;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = seen[timed[i].second];
+        }
+    }
     rc = apply_cfg(s, best);
     if (rc) return rc;
     if (cache) {
