@@ -45,11 +45,19 @@ def _stale(src, obj, hdr_mtime):
     return m < os.path.getmtime(src) or m < hdr_mtime
 
 
+# per-file nvcc flags: the sum-product instantiation flushes fp32 denormals to
+# zero, so its exponentials and logarithms map to the hardware units without
+# denormal fix-ups (its -log weights and exp offsets never need values below
+# 2^-126: rows whose sum of products falls under 1e-20 are recomputed from
+# their raw terms)
+_CU_FLAGS = {"util_kernel_sum.cu": ["-ftz=true"]}
+
+
 def _compile(src, obj, verbose):
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     if src.endswith(".cu"):
         cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-               "-Xcompiler", "-Wall", *inc, "-c", src, "-o", obj]
+               "-Xcompiler", "-Wall", *_CU_FLAGS.get(os.path.basename(src), []), *inc, "-c", src, "-o", obj]
     else:
         cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-Wextra", "-Wno-unused-parameter",
                *inc, "-I", _cuda_include(), "-c", src, "-o", obj]
