@@ -46,8 +46,8 @@ def _stale(src, obj, hdr_mtime):
 
 
 # per-file nvcc flags: the sum-product instantiation flushes fp32 denormals to
-# zero, so its exponentials and logarithms map to the hardware units without
-# denormal fix-ups (its -log weights and exp offsets never need values below
+# zero, which lets its exponentials and logarithms compile to fewer
+# instructions (its -log weights and exp offsets never need values below
 # 2^-126: rows whose sum of products falls under 1e-20 are recomputed from
 # their raw terms)
 _CU_FLAGS = {"util_kernel_sum.cu": ["-ftz=true"]}
