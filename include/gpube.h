@@ -296,11 +296,13 @@ typedef struct gpube_launch_config {
 } gpube_launch_config;
 
 /* Measure candidate launch configurations on this state's own UTIL phase and
- * keep the fastest: CTA size x rows per item, then the lo extent target, the
- * launch mode (per level or one launch over all levels; a per-bucket state
- * keeps its mode), the staging limit, the group-input pipeline and the
- * four-rows-per-thread variant, each
- * varied around the best so far, then the launch shape once more.  Changing
+ * keep the fastest (each candidate: the median of enough runs for about 4 ms
+ * of timing): CTA size x rows per item, then the lo extent target, then two
+ * passes over the launch mode with every lo target (per level or one launch
+ * over all levels; a per-bucket state keeps its mode), the staging limit with
+ * the group-input pipeline on and off, the four-rows-per-thread variant, the
+ * launch shape and the lo target, each varied around the best so far; the
+ * three fastest are timed again with three times the runs.  Changing
  * the lo target or the staging limit re-shapes the tasks and rebuilds the
  * offset tables in the bound arena (candidates that do not fit it are
  * skipped); the tables computed by later runs are unchanged (bit for bit for
