@@ -85,14 +85,20 @@ def test_random_be_all_launch_shapes(orc, seed, shape):
 
 
 @pytest.mark.parametrize("dom", [(1, 3), (2, 2), (3, 3), (5, 5), (7, 8), (9, 10), (9, 12), (16, 16), (2, 8)])
-def test_domain_classes(orc, dom):
-    # every templated domain size (2..8), the generic loop (1, 9..12)
-    inst = synth.random_small(17 + dom[0], n=7, dmin=dom[0], dmax=dom[1], n_funcs=10, max_arity=3)
+@pytest.mark.parametrize("cost_type", ["int", "real"])
+def test_domain_classes(orc, dom, cost_type):
+    # every templated domain size (2..10, 16), the generic loop (1, 11, 12)
+    inst = synth.random_small(17 + dom[0], n=7, dmin=dom[0], dmax=dom[1], n_funcs=10, max_arity=3,
+                              cost_type=cost_type)
     o, _ = orc.minfill(inst)
     run = orc.eliminate(inst, o, "be")
     st, res = run_state(inst, "be", order="given", order_array=o, block_threads=64, lo_target=16)
-    check_tables(inst, st, run)
-    assert res.bound == run.bound and list(res.assignment) == list(run.sigma)
+    check_tables(inst, st, run, exact=(cost_type == "int"))
+    if cost_type == "int":
+        assert res.bound == run.bound and list(res.assignment) == list(run.sigma)
+    else:
+        assert fp_close(res.bound, run.bound)
+        assert fp_close(orc.evaluate(inst, res.assignment), res.cost)
 
 
 @pytest.mark.parametrize("cost_type", ["int", "real"])

@@ -120,7 +120,28 @@ def test_minibucket_sum_bound(orc, mode):
         assert _close(r2.bound, run.bound)
 
 
-@pytest.mark.parametrize("d", [2, 3, 4, 5, 8, 12, 40])
+@pytest.mark.parametrize("d", [2, 3, 5])
+def test_hub_bucket_many_inputs(orc, d):
+    # a hub eliminated first, with ten binary tables to leaves on a chain:
+    # the many-input variant under the sum-product
+    rng = np.random.default_rng(50 + d)
+    n = 11
+    dom = np.full(n, d, dtype=np.int32)
+    scopes = [np.array([0, v], np.int32) for v in range(1, n)] + [np.array([v, v + 1], np.int32) for v in range(1, n - 1)]
+    tables = [-np.log(rng.uniform(0.05, 1.0, size=d * d)) for _ in scopes]
+    inst = synth.Instance("hub", dom, scopes, tables, "real", synth.TOP_K)
+    order = np.arange(n)
+    run = orc.eliminate(inst, order, "be", semiring="sum")
+    for shape in (dict(lo_target=d * d * d, block_threads=32, rows_per_item=4), dict(lo_target=d * d, batched="fused")):
+        st, res = run_state(inst, "sum", order="given", order_array=order, **shape)
+        t0 = st.task(0)
+        assert len(t0["inputs"]) == 10 and t0["n_group"] - t0["n_lo"] <= 8 and 10 - t0["n_group"] <= 2
+        check_sum_tables(st, run)
+        assert _close(res.bound, run.bound)
+        st.free()
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 5, 8, 9, 10, 12, 16, 40])
 def test_domain_classes(orc, d):
     # register variants (d <= 8), the runtime-domain loop (d = 12) and the
     # warp-per-row path (d >= 32)
