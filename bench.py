@@ -248,7 +248,8 @@ def secondary(torch, gb, synth, steps):
                         "util_entries": info["util_entries"], "util_ms": m,
                         "entries_per_s": info["util_entries"] / (m * 1e-3),
                         "gbs": info["alg_bytes"] / (m * 1e-3) / 1e9,
-                        "hbm_frac": info["alg_bytes"] / (m * 1e-3) / 1e9 / peak, "config": mpe_cfg}
+                        "hbm_frac": info["alg_bytes"] / (m * 1e-3) / 1e9 / peak, "config": mpe_cfg,
+                        "argmin_tables": f'{info["n_argmin_tables"]} of {info["n_tasks"]} mini-buckets'}
     # repeated mini-bucket bounds under changing evidence (the bound inside a
     # search): one plan, util_condition + graph replay per bound, against
     # planning and binding a new state per bound (direct launches, the

@@ -138,6 +138,15 @@ typedef struct solve_opts {
                                   a multiple of 4): 16-byte cost stores, 4-byte argmin
                                   stores, block loads of inputs laid out like the output;
                                   0: one row per thread (default)                          */
+    int32_t argmin_tables;     /* 0: argmin tables are written where the VALUE phase reads
+                                  them: BE and DPOP (Algorithm 1, Section 4.1).  The value
+                                  step of Algorithm 2 re-minimises over the functions of
+                                  each bucket and reads none, so a mini-bucket plan leaves
+                                  them out where the kernel has variants without them
+                                  (fp32 costs, domains 2-4, at most 7 inputs) and writes
+                                  the others unread.  The sum-product writes none.
+                                  1: every min-sum task writes its table (to inspect with
+                                  util_fetch_table)                                     */
 } solve_opts;
 
 /* Result of a solve.  assignment, when non-NULL, is caller-owned host memory
@@ -154,9 +163,9 @@ typedef struct solve_result {
     int32_t n_levels;       /* elimination-tree levels                              */
     int32_t n_launches;     /* UTIL kernel launches of one run                      */
     int64_t util_entries;   /* sum over tasks of separator rows x |D_x| (joint rows) */
-    int64_t alg_bytes;      /* 4 x input entries + 5 x output entries, over tasks
-                               (4 x output entries for the sum-product kinds, which
-                               write no argmin tables)                              */
+    int64_t alg_bytes;      /* 4 x input entries + 4 x output entries, over tasks,
+                               + 1 x output entries of the tasks that write an
+                               argmin table (see solve_opts.argmin_tables)          */
     double plan_ms;         /* host planning time                                   */
     double util_ms;         /* device time of the UTIL phase (CUDA events)          */
     double value_ms;        /* device time of the VALUE phase                       */
@@ -170,6 +179,7 @@ typedef struct gpube_plan_info {
     size_t peak_live_bytes;   /* its part that is live at the same time         */
     int32_t max_sep;          /* largest separator                              */
     int32_t max_inputs;       /* most functions in one (mini-)bucket            */
+    int32_t n_argmin_tables;  /* (mini-)buckets that write an argmin table      */
 } gpube_plan_info;
 
 /* One planned (mini-)bucket, for inspection and tests (no GPU needed).
@@ -184,9 +194,10 @@ typedef struct gpube_task_info {
     /* out: work decomposition (rows = groups x r0 x lo_extent); inputs
      * [0, n_lo) depend on the lowest separator digits only, [n_lo, n_group)
      * are read once per group, [n_group, n_uonly) depend on the fastest hi
-     * digit only, the rest are read per row */
+     * digit only, the rest are read per row; argmin = 1 when the task
+     * writes its argmin table */
     int64_t lo_extent, groups;
-    int32_t r0, n_lo, n_group, n_uonly, staged_bytes, pad;
+    int32_t r0, n_lo, n_group, n_uonly, staged_bytes, argmin;
 } gpube_task_info;
 
 typedef struct wcsp wcsp;             /* opaque, library-owned problem         */
@@ -279,7 +290,8 @@ int util_value_launch(util_state *s);
 int util_sync(util_state *s);
 
 /* Copy one task's output (cost table and argmin table, rows entries each) to
- * host buffers (either may be NULL); synchronous. */
+ * host buffers (either may be NULL); synchronous.  For a task that writes no
+ * argmin table (solve_opts.argmin_tables) arg_host receives zeros. */
 int util_fetch_table(util_state *s, int32_t t, void *cost_host, uint8_t *arg_host);
 
 /* The launch configuration of a state (what util_autotune chooses). */

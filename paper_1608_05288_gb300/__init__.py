@@ -105,7 +105,8 @@ LAUNCH_MODES = {"bucket": 0, "level": 1, "fused": 2}
 def make_opts(order="minfill", order_array=None, parent=None, ibound_mode="sep", batched=True,
               use_graph=False, block_threads=0, rows_per_item=0, lo_target=0,
               stage_max_entries=0, arena=None, arena_bytes=0, stream=None,
-              autotune_cache=None, device=0, evidence_vars=None, pipeline=True, vector_rows=False):
+              autotune_cache=None, device=0, evidence_vars=None, pipeline=True, vector_rows=False,
+              argmin_tables=False):
     o = _abi.SolveOpts()
     lib().solve_opts_init(C.byref(o))
     o.order_kind = ORDERS[order] if isinstance(order, str) else int(order)
@@ -139,6 +140,9 @@ def make_opts(order="minfill", order_array=None, parent=None, ibound_mode="sep",
     o.device = int(device)
     o.pipeline = 0 if pipeline else -1
     o.vector_rows = 1 if vector_rows else 0
+    # argmin tables of mini-bucket plans (their value step reads none): written
+    # only when asked for
+    o.argmin_tables = 1 if argmin_tables else 0
     if evidence_vars is not None and len(evidence_vars):
         ev = _i32(evidence_vars)
         keep.append(ev)
@@ -261,7 +265,7 @@ class UtilState:
         return {"var": ti.var, "level": ti.level, "rows": ti.rows, "sep": sep[: ti.n_sep].copy(),
                 "inputs": ins[: ti.n_inputs].copy(), "lo_extent": ti.lo_extent, "groups": ti.groups,
                 "r0": ti.r0, "n_lo": ti.n_lo, "n_group": ti.n_group, "n_uonly": ti.n_uonly,
-                "staged_bytes": ti.staged_bytes}
+                "staged_bytes": ti.staged_bytes, "argmin": bool(ti.argmin)}
 
     def tasks(self):
         return [self.task(t) for t in range(self.info()["n_tasks"])]

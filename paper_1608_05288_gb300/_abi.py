@@ -32,7 +32,7 @@ class SolveOpts(C.Structure):
                 ("arena", C.c_void_p), ("arena_bytes", C.c_size_t), ("stream", C.c_void_p),
                 ("autotune_cache", C.c_char_p), ("device", C.c_int32),
                 ("evidence_vars", i32p), ("n_evidence_vars", C.c_int32), ("pipeline", C.c_int32),
-                ("vector_rows", C.c_int32)]
+                ("vector_rows", C.c_int32), ("argmin_tables", C.c_int32)]
 
 
 class LaunchConfig(C.Structure):
@@ -53,7 +53,7 @@ class PlanInfo(C.Structure):
                 ("induced_width", C.c_int32), ("util_entries", C.c_int64),
                 ("out_entries", C.c_int64), ("in_entries", C.c_int64), ("alg_bytes", C.c_int64),
                 ("arena_bytes", C.c_size_t), ("peak_live_bytes", C.c_size_t),
-                ("max_sep", C.c_int32), ("max_inputs", C.c_int32)]
+                ("max_sep", C.c_int32), ("max_inputs", C.c_int32), ("n_argmin_tables", C.c_int32)]
 
 
 class TaskInfo(C.Structure):
@@ -61,7 +61,7 @@ class TaskInfo(C.Structure):
                 ("n_inputs", C.c_int32), ("rows", C.c_int64), ("sep", i32p), ("inputs", i32p),
                 ("lo_extent", C.c_int64), ("groups", C.c_int64), ("r0", C.c_int32), ("n_lo", C.c_int32),
                 ("n_group", C.c_int32), ("n_uonly", C.c_int32), ("staged_bytes", C.c_int32),
-                ("pad", C.c_int32)]
+                ("argmin", C.c_int32)]
 
 
 # name -> (restype, argtypes)

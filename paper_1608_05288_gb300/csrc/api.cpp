@@ -274,7 +274,7 @@ void gpube_layout(util_state *s)
         T.out_off = T.ext_out ? 0 : c.take(T.rows * 4, 128);
         P.funcs[w.nf + t].off = T.out_off;
     }
-    for (Task &T : P.tasks) T.arg_off = T.ext_arg ? 0 : c.take(T.rows, 128);
+    for (Task &T : P.tasks) T.arg_off = (T.ext_arg || !T.keep_arg) ? 0 : c.take(T.rows, 128);
     for (Task &T : P.tasks) {
         T.A_off = c.take(static_cast<size_t>(T.G + 1) * T.sa * 4, 128);
         T.B_off = c.take(static_cast<size_t>(T.P_lo) * T.sb * 4, 128);
@@ -328,7 +328,8 @@ void gpube_layout(util_state *s)
     // tables of BE / DPOP messages are released once their bucket is done
     size_t fixed = s->upload_bytes + (s->arena_bytes - s->desc_off);
     size_t live = fixed, peak = fixed;
-    for (const Task &T : P.tasks) live += al(T.rows, 128) + al((T.G + 1) * T.sa * 4, 128) + al(T.P_lo * T.sb * 4, 128);
+    for (const Task &T : P.tasks)
+        live += (T.keep_arg ? al(T.rows, 128) : 0) + al((T.G + 1) * T.sa * 4, 128) + al(T.P_lo * T.sb * 4, 128);
     peak = live;
     for (const Task &T : P.tasks) {
         live += al(T.rows * 4, 128);
@@ -453,6 +454,8 @@ extern "C" int util_plan_info(const util_state *s, gpube_plan_info *info)
     info->peak_live_bytes = P.peak_live_bytes;
     info->max_sep = P.width;
     info->max_inputs = P.max_inputs;
+    info->n_argmin_tables = 0;
+    for (const Task &T : P.tasks) info->n_argmin_tables += T.keep_arg ? 1 : 0;
     return GPUBE_OK;
 }
 
@@ -475,7 +478,7 @@ extern "C" int util_task_info(const util_state *s, int32_t t, gpube_task_info *i
     info->n_group = T.n_gi;
     info->n_uonly = T.n_uo;
     info->staged_bytes = T.stage_bytes;
-    info->pad = 0;
+    info->argmin = T.keep_arg ? 1 : 0;
     return GPUBE_OK;
 }
 
@@ -555,7 +558,8 @@ int gpube_build_descriptors(util_state *s)
         x.B = reinterpret_cast<const int32_t *>(B + T.B_off);
         x.in = reinterpret_cast<const InDev *>(B + D.indev) + in_pos;
         x.out = T.ext_out ? T.ext_out : static_cast<void *>(B + T.out_off);
-        x.arg = T.ext_arg ? T.ext_arg : B + T.arg_off;
+        // (null only for shapes whose kernel variants leave the argmin out)
+        x.arg = !T.keep_arg ? nullptr : T.ext_arg ? T.ext_arg : B + T.arg_off;
         x.F = static_cast<int32_t>(T.inputs.size());
         x.d = T.d;
         x.sa = T.sa;
@@ -1142,7 +1146,10 @@ extern "C" int util_fetch_table(util_state *s, int32_t t, void *cost_host, uint8
     const Task &T = s->plan.tasks[t];
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     if (cost_host) CUDA_TRY(cudaMemcpy(cost_host, s->base + T.out_off, T.rows * 4, cudaMemcpyDeviceToHost));
-    if (arg_host) CUDA_TRY(cudaMemcpy(arg_host, s->base + T.arg_off, T.rows, cudaMemcpyDeviceToHost));
+    if (arg_host) {
+        if (T.keep_arg) CUDA_TRY(cudaMemcpy(arg_host, s->base + T.arg_off, T.rows, cudaMemcpyDeviceToHost));
+        else memset(arg_host, 0, static_cast<size_t>(T.rows));  // the task keeps no argmin table
+    }
     return GPUBE_OK;
 }
 

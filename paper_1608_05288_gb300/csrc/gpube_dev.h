@@ -65,7 +65,7 @@ struct alignas(16) TaskDev {
     const int32_t *B;    // [P_lo][sb]
     const InDev *in;     // [F]
     void *out;           // [rows] int32 or float
-    uint8_t *arg;        // [rows]
+    uint8_t *arg;        // [rows] argmins; null when none is kept (fp32 min-sum, d 2-4, F <= 7 only)
     int32_t F, d, sa, sb;
     int32_t P_lo, G, hc, nlc;  // hc = groups per item; nlc = lo chunks (blockDim.x rows, or blockDim.x / 32 for wide domains)
     int32_t variant;           // dclass * kNumFClass + fclass

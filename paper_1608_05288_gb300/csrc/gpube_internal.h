@@ -92,6 +92,7 @@ struct Task {
     uint8_t *ext_arg = nullptr;
     std::vector<int32_t> stage_off;  // per input: shared-memory byte offset or -1
     int32_t stage_bytes = 0;
+    bool keep_arg = true;            // its argmin table is written
 };
 
 // Mini-bucket partition (Algorithm 2) / sum-product elimination, by kind.
@@ -116,16 +117,33 @@ struct Plan {
     bool allow_pipe = true;   // group runs prefetched by the per-thread cp.async pipeline (KP groups in
                               // flight) where a task allows it; false: register variants (1-2 groups)
     bool allow_v4 = false;    // four consecutive rows per thread where a task allows it
+    bool keep_arg = true;     // argmin tables asked for: the VALUE phase of BE and DPOP reads
+                              // them (mini-bucket plans re-minimise over the bucket's
+                              // functions instead) or solve_opts.argmin_tables
     size_t peak_live_bytes = 0;
     ValuePlanH value;
 };
 
+// Whether a task writes its argmin table: never for the sum-product, always
+// when the plan asks for them, and otherwise unless the kernel has variants
+// that leave the argmin out for the task's shape (fp32 min-sum, domains 2-4,
+// at most 7 inputs); other shapes write theirs, unread.
+inline bool task_keeps_arg(int cost_type, const Plan &P, const Task &T)
+{
+    if (kind_sum(P.kind)) return false;
+    if (P.keep_arg) return true;
+    return !(cost_type == WCSP_FP32_LOG && T.d >= 2 && T.d <= 4 && T.inputs.size() <= 7);
+}
+
 // Algorithmic bytes of a plan: every input entry read once (4 bytes), every
-// output entry written once (4 bytes) with its argmin (1 byte; the
-// sum-product kinds write no argmin).
+// output entry written once (4 bytes) with its argmin where the task keeps
+// its argmin table (1 byte).
 inline int64_t alg_bytes_of(const Plan &P)
 {
-    return 4 * P.in_entries + (kind_sum(P.kind) ? 4 : 5) * P.out_entries;
+    int64_t arg_bytes = 0;
+    for (const Task &T : P.tasks)
+        if (T.keep_arg) arg_bytes += T.rows;
+    return 4 * P.in_entries + 4 * P.out_entries + arg_bytes;
 }
 
 // Launch parameters of one run.

@@ -309,6 +309,7 @@ int build_plan(const wcsp &w, int kind, int i_bound, const int32_t *parent, cons
     if (o.stage_max_entries < 0) P.stage_max_entries = 0;
     P.allow_pipe = o.pipeline >= 0;
     P.allow_v4 = o.vector_rows > 0;
+    P.keep_arg = !kind_mbe(kind) || o.argmin_tables > 0;
 
     // 1. elimination order
     int okind = o.order_kind;
@@ -597,6 +598,7 @@ void shape_tasks(const wcsp &w, Plan &P)
             T.stage_off[f] = T.stage_bytes;
             T.stage_bytes += static_cast<int32_t>(bytes);
         }
+        T.keep_arg = task_keeps_arg(w.cost_type, P, T);
     }
 }
 

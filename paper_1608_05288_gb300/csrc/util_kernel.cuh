@@ -342,7 +342,7 @@ __device__ __forceinline__ void load_ints(const int32_t *p, int32_t (&a)[N])
 // input): the lo-only inputs are summed once per item, the group inputs once
 // per group, and each row adds only the inputs that mention the fastest hi
 // digit u.
-template <typename C, int D>
+template <typename C, int D, bool WA = true>
 __device__ __noinline__ void item_fixed_anyF(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo,
                                                 int g0, int g1, uint32_t k)
 {
@@ -387,7 +387,7 @@ __device__ __noinline__ void item_fixed_anyF(const TaskDev *__restrict__ tkp, co
             const A best = reduce_run<C, D>(acc, bi);
             const int o = Ar[0] + u * du[0] + lo;
             out[o] = C::store(best);
-            if constexpr (!C::kSum) tk.arg[o] = static_cast<uint8_t>(bi);
+            if constexpr (!C::kSum && WA) tk.arg[o] = static_cast<uint8_t>(bi);
         }
     }
 }
@@ -477,8 +477,9 @@ __device__ __noinline__ void item_fixed_manyF(const TaskDev *__restrict__ tkp, c
 // both.  Row offsets advance by the stride of u: a row costs NR vector
 // loads, the adds, the argmin and two stores.  U > 0: the radix R0 of u is
 // U, and the per-row runs of all U rows of the NG groups are loaded before
-// any of them is summed (U x NG x NR loads in flight per thread).
-template <typename C, int D, int FC, int NR, int U = 0>
+// any of them is summed (U x NG x NR loads in flight per thread).  WA =
+// false: a variant that writes no argmin table (for tasks whose arg is null).
+template <typename C, int D, int FC, int NR, int U = 0, bool WA = true>
 __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo, int g0,
                                               int g1, uint32_t k)
 {
@@ -580,7 +581,7 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
                         const A best = reduce_run<C, D>(acc, bi);
                         const int32_t o = oo[j] + u * d0;
                         out[o] = C::store(best);
-                        if constexpr (!C::kSum) arg[o] = static_cast<uint8_t>(bi);
+                        if constexpr (!C::kSum && WA) arg[o] = static_cast<uint8_t>(bi);
                     }
         } else {
             for (int u = 0; u < R0; ++u) {
@@ -601,7 +602,7 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
                         int bi;
                         const A best = reduce_run<C, D>(acc, bi);
                         out[oo[j]] = C::store(best);
-                        if constexpr (!C::kSum) arg[oo[j]] = static_cast<uint8_t>(bi);
+                        if constexpr (!C::kSum && WA) arg[oo[j]] = static_cast<uint8_t>(bi);
                         oo[j] += d0;
                     }
                 }
@@ -628,8 +629,8 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
 // partial sums are kept as keys (s << 2 | l) and the group run as (x << 2),
 // so a row's sums are D adds of keys, its minimum and first argmin one
 // unsigned min over them (equal sums: the lower l has the lower key), and no
-// saturation is needed.
-template <typename C, int D, int NRG, bool FOLD, int U = 0, bool PK = false>
+// saturation is needed.  WA = false: no argmin table is written.
+template <typename C, int D, int NRG, bool FOLD, int U = 0, bool PK = false, bool WA = true>
 __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const unsigned char *stage, unsigned char *pipe,
                                           const int32_t *arows, int lo, int g0, int g1, uint32_t k)
 {
@@ -638,7 +639,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     using A = typename C::acc;
     constexpr bool kInt = std::is_same<T, int32_t>::value;
     static_assert(!PK || (kInt && FOLD && NRG == 0 && U > 0 && D <= 4), "packed keys: integer rows of two terms");
-    constexpr int FC = 3, SA = 4, SB = 4, UMAX = 4;
+    constexpr int SA = 4, SB = 4, UMAX = 4;  // at most 3 inputs: A and B rows of 4 ints
     constexpr int R = NRG > 0 ? NRG : 1;
     constexpr int CH = (D % 4 == 0) ? 16 : (D % 2 == 0) ? 8 : 4;  // bytes per copy
     constexpr int NCH = D * 4 / CH;                                  // copies per run
@@ -774,7 +775,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
             }
         }
         out[o] = C::store(best);
-        if constexpr (!C::kSum) arg[o] = static_cast<uint8_t>(bi);
+        if constexpr (!C::kSum && WA) arg[o] = static_cast<uint8_t>(bi);
     };
     // one output row: b (partial sum) + x (group run) + the NRG per-row runs
     auto row = [&](const A (&b)[D], const T (&x)[D], int32_t (&ro)[R], int32_t o) {
@@ -847,7 +848,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
 #pragma unroll
                 for (int l = 1; l < D; ++l) m = min(m, bur[u][l] + xs[l]);
                 out[o] = static_cast<T>(m >> 2);
-                arg[o] = static_cast<uint8_t>(m & 3u);
+                if constexpr (WA) arg[o] = static_cast<uint8_t>(m & 3u);
                 o += d0;
             }
             issue(g + KP, slot);  // the slot's data has been consumed
@@ -920,7 +921,7 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
 //     (L1-resident), so that no per-row offsets are held in registers.
 // Inputs [0, n_gi) mention no u and are summed once per group, the others
 // once per row.
-template <typename C, int D>
+template <typename C, int D, bool WA = true>
 __device__ __noinline__ void item_v4(const TaskDev *__restrict__ tkp, const unsigned char *stage, int lo4, int g0,
                                      int g1, uint32_t k)
 {
@@ -1008,7 +1009,7 @@ __device__ __noinline__ void item_v4(const TaskDev *__restrict__ tkp, const unsi
             }
             using V4 = typename std::conditional<std::is_same<T, float>::value, float4, int4>::type;
             *reinterpret_cast<V4 *>(out + o) = V4{best[0], best[1], best[2], best[3]};
-            if constexpr (!C::kSum) *reinterpret_cast<uint32_t *>(arg + o) = bi;
+            if constexpr (!C::kSum && WA) *reinterpret_cast<uint32_t *>(arg + o) = bi;
             o += du[0];
 #pragma unroll
             for (int f = 0; f < FC; ++f) h[f] += du[1 + f];
@@ -1016,14 +1017,14 @@ __device__ __noinline__ void item_v4(const TaskDev *__restrict__ tkp, const unsi
     }
 }
 
-template <typename C, int D, int FC>
+template <typename C, int D, int FC, bool WA = true>
 __device__ __forceinline__ void item_fixed(const TaskDev *__restrict__ tkp, const TaskDev &tk,
                                            const unsigned char *stage, unsigned char *pipe, const int32_t *arows,
                                            int lo, int g0, int g1, uint32_t k)
 {
     if constexpr (FC <= 3 && D <= 3) {
         if (tk.v4) {
-            item_v4<C, D>(tkp, stage, lo, g0, g1, k);
+            item_v4<C, D, WA>(tkp, stage, lo, g0, g1, k);
             return;
         }
     }
@@ -1034,67 +1035,67 @@ __device__ __forceinline__ void item_fixed(const TaskDev *__restrict__ tkp, cons
                 case 0:  // the radix of u as a template constant: unrolled rows, partial sums in registers
                     if constexpr (std::is_same<C, Cost<int32_t>>::value && D <= 4) {
                         if (tk.nosat && tk.R0 >= 2) {  // sums below the top cost: packed keys
-                            if (tk.R0 == 4) item_pipe<C, D, 0, true, 4, true>(tkp, stage, pipe, arows, lo, g0, g1, k);
-                            else if (tk.R0 == 3) item_pipe<C, D, 0, true, 3, true>(tkp, stage, pipe, arows, lo, g0, g1, k);
-                            else item_pipe<C, D, 0, true, 2, true>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                            if (tk.R0 == 4) item_pipe<C, D, 0, true, 4, true, WA>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                            else if (tk.R0 == 3) item_pipe<C, D, 0, true, 3, true, WA>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                            else item_pipe<C, D, 0, true, 2, true, WA>(tkp, stage, pipe, arows, lo, g0, g1, k);
                             break;
                         }
                     }
-                    if (tk.R0 == 4) item_pipe<C, D, 0, true, 4>(tkp, stage, pipe, arows, lo, g0, g1, k);
-                    else if (tk.R0 == 3) item_pipe<C, D, 0, true, 3>(tkp, stage, pipe, arows, lo, g0, g1, k);
-                    else if (tk.R0 == 2) item_pipe<C, D, 0, true, 2>(tkp, stage, pipe, arows, lo, g0, g1, k);
-                    else item_pipe<C, D, 0, true>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    if (tk.R0 == 4) item_pipe<C, D, 0, true, 4, false, WA>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    else if (tk.R0 == 3) item_pipe<C, D, 0, true, 3, false, WA>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    else if (tk.R0 == 2) item_pipe<C, D, 0, true, 2, false, WA>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    else item_pipe<C, D, 0, true, 0, false, WA>(tkp, stage, pipe, arows, lo, g0, g1, k);
                     break;
                 case 1:  // one per-row input: its runs for the U rows loaded together
                          // (domains up to 4; larger ones would spill them)
                     if constexpr (D <= 4) {
                         if (tk.R0 == 2) {
-                            item_pipe<C, D, 1, true, 2>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                            item_pipe<C, D, 1, true, 2, false, WA>(tkp, stage, pipe, arows, lo, g0, g1, k);
                             break;
                         }
                         if (tk.R0 == 3) {
-                            item_pipe<C, D, 1, true, 3>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                            item_pipe<C, D, 1, true, 3, false, WA>(tkp, stage, pipe, arows, lo, g0, g1, k);
                             break;
                         }
                         if (tk.R0 == 4) {
-                            item_pipe<C, D, 1, true, 4>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                            item_pipe<C, D, 1, true, 4, false, WA>(tkp, stage, pipe, arows, lo, g0, g1, k);
                             break;
                         }
                     }
-                    item_pipe<C, D, 1, true>(tkp, stage, pipe, arows, lo, g0, g1, k);
+                    item_pipe<C, D, 1, true, 0, false, WA>(tkp, stage, pipe, arows, lo, g0, g1, k);
                     break;
-                default: item_pipe<C, D, 2, true>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                default: item_pipe<C, D, 2, true, 0, false, WA>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
                 }
             } else {
                 switch (tk.F - tk.n_gi) {
-                case 0: item_pipe<C, D, 0, false>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
-                case 1: item_pipe<C, D, 1, false>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
-                default: item_pipe<C, D, 2, false>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                case 0: item_pipe<C, D, 0, false, 0, false, WA>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                case 1: item_pipe<C, D, 1, false, 0, false, WA>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
+                default: item_pipe<C, D, 2, false, 0, false, WA>(tkp, stage, pipe, arows, lo, g0, g1, k); break;
                 }
             }
             return;
         }
     }
     switch (tk.F - tk.n_gi) {
-    case 0: item_fixed_nr<C, D, FC, 0>(tkp, stage, lo, g0, g1, k); break;
+    case 0: item_fixed_nr<C, D, FC, 0, 0, WA>(tkp, stage, lo, g0, g1, k); break;
     case 1:  // one per-row input: the rows of u unrolled for small radices and
              // domains (larger ones would spill the loaded runs)
         if constexpr (D <= 3) {
             if (tk.R0 == 2) {
-                item_fixed_nr<C, D, FC, 1, 2>(tkp, stage, lo, g0, g1, k);
+                item_fixed_nr<C, D, FC, 1, 2, WA>(tkp, stage, lo, g0, g1, k);
                 break;
             }
             if (tk.R0 == 3) {
-                item_fixed_nr<C, D, FC, 1, 3>(tkp, stage, lo, g0, g1, k);
+                item_fixed_nr<C, D, FC, 1, 3, WA>(tkp, stage, lo, g0, g1, k);
                 break;
             }
         }
-        item_fixed_nr<C, D, FC, 1>(tkp, stage, lo, g0, g1, k);
+        item_fixed_nr<C, D, FC, 1, 0, WA>(tkp, stage, lo, g0, g1, k);
         break;
-    case 2: item_fixed_nr<C, D, FC, 2>(tkp, stage, lo, g0, g1, k); break;
+    case 2: item_fixed_nr<C, D, FC, 2, 0, WA>(tkp, stage, lo, g0, g1, k); break;
     default:
-        if constexpr (FC <= 3) item_fixed_nr<C, D, FC, 3>(tkp, stage, lo, g0, g1, k);
-        else item_fixed_anyF<C, D>(tkp, stage, lo, g0, g1, k);
+        if constexpr (FC <= 3) item_fixed_nr<C, D, FC, 3, 0, WA>(tkp, stage, lo, g0, g1, k);
+        else item_fixed_anyF<C, D, WA>(tkp, stage, lo, g0, g1, k);
         break;
     }
 }
@@ -1338,9 +1339,29 @@ __device__ __forceinline__ void dispatch_f(const TaskDev *__restrict__ tkp, cons
         default: item_anyD_anyF<C>(tkp, stage, lo, h0, h1, k); break;
         }
     } else {
+        // fp32 min-sum with domains up to 4 (the -log p mini-bucket bounds,
+        // whose plans keep no argmin tables) has variants that leave the
+        // argmin out altogether
+        constexpr bool kNoArg = std::is_same<C, Cost<float>>::value && D <= 4;
         switch (fc) {
-        case 0: item_fixed<C, D, 3>(tkp, tk, stage, pipe, arows, lo, h0, h1, k); break;
-        case 1: item_fixed<C, D, 7>(tkp, tk, stage, pipe, arows, lo, h0, h1, k); break;
+        case 0:
+            if constexpr (kNoArg) {
+                if (!tk.arg) {
+                    item_fixed<C, D, 3, false>(tkp, tk, stage, pipe, arows, lo, h0, h1, k);
+                    break;
+                }
+            }
+            item_fixed<C, D, 3>(tkp, tk, stage, pipe, arows, lo, h0, h1, k);
+            break;
+        case 1:
+            if constexpr (kNoArg) {
+                if (!tk.arg) {
+                    item_fixed<C, D, 7, false>(tkp, tk, stage, pipe, arows, lo, h0, h1, k);
+                    break;
+                }
+            }
+            item_fixed<C, D, 7>(tkp, tk, stage, pipe, arows, lo, h0, h1, k);
+            break;
         default:
             if constexpr (D <= 10) {
                 if (tk.n_gi - tk.n_lo <= 8 && tk.F - tk.n_gi <= 2) {

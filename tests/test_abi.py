@@ -212,6 +212,35 @@ def test_sum_counting_plan_of_integer_wcsp(orc):
     assert i_sm["alg_bytes"] == i_be["alg_bytes"] - i_be["out_entries"]
 
 
+@pytest.mark.parametrize("cost_type", ["int", "real"])
+def test_argmin_tables_only_where_the_value_phase_reads_them(cost_type):
+    # BE and DPOP look their assignment up in argmin tables (Algorithm 1,
+    # Section 4.1); the value step of Algorithm 2 re-minimises over each
+    # bucket's functions, so a mini-bucket plan leaves a task's table out
+    # where the kernel has variants without it (fp32 costs, domains 2-4, at
+    # most 7 inputs) unless asked for them; the sum-product writes none
+    inst = synth.random_small(11, n=14, dmax=6, n_funcs=22, max_arity=3, cost_type=cost_type)
+    states = {k: gb.UtilState(inst, k, 2) for k in ("be", "dpop", "sum", "mbe")}
+    states["mbe_arg"] = gb.UtilState(inst, "mbe", 2, argmin_tables=True)
+    info = {k: s.info() for k, s in states.items()}
+    for k in ("be", "dpop", "mbe_arg"):
+        assert info[k]["n_argmin_tables"] == info[k]["n_tasks"]
+    assert info["sum"]["n_argmin_tables"] == 0
+    tasks = states["mbe"].tasks()
+    without = [t for t in tasks if cost_type == "real" and 2 <= inst.dom[t["var"]] <= 4 and len(t["inputs"]) <= 7]
+    assert [not t["argmin"] for t in tasks] == [t in without for t in tasks]
+    if cost_type == "real":
+        assert without and len(without) < len(tasks)  # the instance has both kinds of task
+    mb, mb_arg = info["mbe"], info["mbe_arg"]
+    assert mb["n_argmin_tables"] == len(tasks) - len(without)
+    assert mb["out_entries"] == mb_arg["out_entries"] and mb["in_entries"] == mb_arg["in_entries"]
+    kept = sum(t["rows"] for t in tasks if t["argmin"])
+    assert mb["alg_bytes"] == 4 * mb["in_entries"] + 4 * mb["out_entries"] + kept
+    assert mb_arg["alg_bytes"] == 4 * mb_arg["in_entries"] + 5 * mb_arg["out_entries"]
+    # a table left out takes no arena space
+    assert mb["arena_bytes"] + sum(t["rows"] for t in without) <= mb_arg["arena_bytes"]
+
+
 def test_evidence_plan_matches_oracle(orc):
     # evidence variables add one unary function each, after the problem's own
     inst = synth.random_small(11, n=10, dmax=4, n_funcs=14, max_arity=3)

@@ -44,7 +44,7 @@ def _case(seed):
                  lo_target=int(rng.choice([1, 5, 64, 2048])),
                  stage_max_entries=int(rng.choice([-1, 4, 0])),
                  use_graph=bool(rng.random() < 0.5), batched=int(rng.choice([0, 1, 1, 2, 2])),
-                 vector_rows=bool(rng.random() < 0.4))
+                 vector_rows=bool(rng.random() < 0.4), argmin_tables=bool(rng.random() < 0.5))
     return inst, kind, mode, z, shape
 
 
@@ -58,14 +58,24 @@ def test_random_configuration(orc, seed):
     st, res = run_state(inst, kind, z, order="given", order_array=o, ibound_mode=mode, **shape)
     assert structure(st) == orc_structure(run)
     exact = inst.cost_type == "int" and semiring == "min"
+    tasks = st.tasks()
     for t, T in enumerate(run.tasks):
+        # BE always writes its argmin tables, the sum-product never, MBE when
+        # asked or where the kernel has no variant without them
+        keeps = tasks[t]["argmin"]
+        d, F = int(inst.dom[T.var]), len(tasks[t]["inputs"])
+        assert keeps == (kind == "be" or (kind == "mbe" and (shape["argmin_tables"] or exact or not 2 <= d <= 4
+                                                              or F > 7)))
         cost, arg = st.fetch(t)
+        if not keeps:
+            assert not np.any(arg), f"task {t}"
         if exact:
             assert np.array_equal(cost.astype(np.int64), T.out.astype(np.int64)), f"task {t}"
-            assert np.array_equal(arg, T.arg), f"task {t}"
+            if keeps:
+                assert np.array_equal(arg, T.arg), f"task {t}"
         else:
             assert fp_close(cost, T.out), f"task {t}"
-            if semiring == "min":  # fp32 min-sum: the argmin attains the minimum
+            if keeps:  # fp32 min-sum: the argmin attains the minimum
                 assert argmin_attains_minimum(inst, run, t, arg), f"task {t} argmin"
     if exact:
         assert res.bound == run.bound and res.cost == run.cost

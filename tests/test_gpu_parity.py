@@ -44,7 +44,7 @@ def test_paper_example(orc):
     inst = synth.paper_example()
     order = np.array([3, 2, 1, 0])
     for kind, mode, z in (("be", "be", 0), ("mbe", "sep", 1)):
-        st, res = run_state(inst, kind, z, order="given", order_array=order, ibound_mode="sep")
+        st, res = run_state(inst, kind, z, order="given", order_array=order, ibound_mode="sep", argmin_tables=True)
         run = orc.eliminate(inst, order, mode, z)
         check_tables(inst, st, run)
         assert res.bound == run.bound and res.cost == run.cost
@@ -61,12 +61,14 @@ def test_mbe_value_golden():
     dom = np.array(g["dom"], dtype=np.int32)
     inst = synth.Instance("mbe_value", dom, [np.array(x, dtype=np.int32) for x in g["scopes"]],
                           [np.array(t, dtype=np.int64) for t in g["tables"]], "int", 1 << 30)
-    for shape in LAUNCH_SHAPES[:3]:
+    for shape, keep in ((s, k) for s in LAUNCH_SHAPES[:3] for k in (True, False)):
         st, res = run_state(inst, "mbe", g["z"], order="given", order_array=g["order"], ibound_mode=g["mode"],
-                            **shape)
+                            argmin_tables=keep, **shape)
         for t, T in enumerate(g["tasks"]):
             cost, arg = st.fetch(t)
-            assert [int(x) for x in cost] == T["out"] and [int(x) for x in arg] == T["arg"], t
+            assert [int(x) for x in cost] == T["out"], t
+            assert st.task(t)["argmin"]  # integer costs: every task writes its table
+            assert [int(x) for x in arg] == T["arg"], t
         assert res.bound == g["bound"] and res.cost == g["cost"]
         assert list(res.assignment) == g["sigma"]
         st.free()
@@ -151,17 +153,47 @@ def test_many_inputs(orc, nf):
     assert res.bound == run.bound
 
 
+@pytest.mark.parametrize("keep", [False, True])
 @pytest.mark.parametrize("mode", ["sep", "joint", "log2"])
-def test_random_mbe(orc, mode):
+def test_random_mbe(orc, mode, keep):
     for seed in range(4):
         inst = synth.random_small(seed + 300, n=11, dmax=4, n_funcs=18, max_arity=3)
         o, _ = orc.minfill(inst)
         for z in (1, 2, 4):
             run = orc.eliminate(inst, o, mode, z)
-            st, res = run_state(inst, "mbe", z, order="given", order_array=o, ibound_mode=mode)
+            st, res = run_state(inst, "mbe", z, order="given", order_array=o, ibound_mode=mode, argmin_tables=keep)
             check_tables(inst, st, run)
             assert res.bound == run.bound and res.cost == run.cost
             assert list(res.assignment) == list(run.sigma)
+
+
+@pytest.mark.parametrize("cost_type", ["int", "real"])
+def test_mbe_without_argmin_tables(orc, cost_type):
+    # mini-bucket plans write no argmin tables by default (their value step
+    # re-minimises over each bucket's functions): the same bucket functions,
+    # bound and assignment as with the tables, in every launch form
+    for seed in range(3):
+        inst = synth.random_small(seed + 510, n=12, dmax=3, n_funcs=20, max_arity=3, cost_type=cost_type)
+        o, _ = orc.minfill(inst)
+        for z, mode in ((2, "sep"), (3, "joint"), (5, "log2")):
+            for shape in (dict(), dict(batched=False), dict(batched="fused", use_graph=True),
+                          dict(vector_rows=True), dict(block_threads=32, rows_per_item=3, lo_target=4)):
+                a, ra = run_state(inst, "mbe", z, order="given", order_array=o, ibound_mode=mode, **shape)
+                b, rb = run_state(inst, "mbe", z, order="given", order_array=o, ibound_mode=mode,
+                                  argmin_tables=True, **shape)
+                assert b.info()["n_argmin_tables"] == len(b.tasks())
+                ta = a.tasks()
+                for t in range(len(ta)):
+                    ca, aa = a.fetch(t)
+                    cb, ab = b.fetch(t)
+                    assert np.array_equal(ca, cb), (seed, z, t)
+                    assert np.array_equal(aa, ab) if ta[t]["argmin"] else not np.any(aa), (seed, z, t)
+                if cost_type == "real":
+                    assert not all(t["argmin"] for t in ta)  # some tasks leave the table out
+                assert ra.bound == rb.bound and list(ra.assignment) == list(rb.assignment)
+                assert ra.cost == rb.cost or (np.isnan(ra.cost) and np.isnan(rb.cost))
+                a.free()
+                b.free()
 
 
 def test_saturation_and_infeasible(orc):
@@ -216,8 +248,8 @@ def test_config2_mbe_full(orc):
     inst = synth.config_instance(2, 0)
     o, _ = orc.minfill(inst)
     run = orc.eliminate(inst, o, "log2", 16)
-    for shape in (dict(use_graph=True), dict(batched=False), dict(batched="fused", use_graph=True),
-                  dict(vector_rows=True, use_graph=True)):
+    for shape in (dict(use_graph=True, argmin_tables=True), dict(batched=False), dict(batched="fused", use_graph=True),
+                  dict(vector_rows=True, use_graph=True, argmin_tables=True)):
         st, res = run_state(inst, "mbe", 16, ibound_mode="log2", **shape)
         check_tables(inst, st, run)
         assert res.bound == run.bound and res.cost == run.cost
@@ -232,7 +264,7 @@ def test_config3_mpe_mbe_and_exact_prefix(orc):
         run = orc.eliminate(inst, o, "sep", 20)
     finally:
         orc.set_threads(1)
-    for shape in (dict(use_graph=True), dict(batched="fused", use_graph=True, vector_rows=True)):
+    for shape in (dict(use_graph=True), dict(batched="fused", use_graph=True, vector_rows=True, argmin_tables=True)):
         st, res = run_state(inst, "mbe", 20, ibound_mode="sep", **shape)
         check_tables(inst, st, run, exact=False)
         assert fp_close(res.bound, run.bound)
