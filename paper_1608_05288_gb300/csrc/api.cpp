@@ -490,6 +490,29 @@ extern "C" int util_order(const util_state *s, int32_t *order)
 }
 
 // ------------------------------------------------------------ descriptors
+// Distinct runs of input f that the first `lanes` rows of a lo chunk (one
+// warp) read.  The cp.async pipeline copies every lane's run on its own, and
+// copies of one global address into many lanes' slots take several
+// shared-memory wavefronts each (on GB300 about 11 per instruction when 4-8
+// distinct runs feed a warp), so an input that a warp reads mostly
+// duplicated is read with plain loads instead, which broadcast.
+static int warp_distinct_runs(const wcsp &w, const Task &T, const std::vector<int32_t> &st, int f, int lanes)
+{
+    const int m = static_cast<int>(T.sep.size());
+    std::vector<int64_t> off(static_cast<size_t>(lanes));
+    for (int lo = 0; lo < lanes; ++lo) {
+        int64_t r = lo, o = 0;
+        for (int j = m - 1; j >= m - T.L; --j) {
+            const int dj = w.dom[T.sep[j]];
+            o += (r % dj) * st[static_cast<size_t>(f) * m + j];
+            r /= dj;
+        }
+        off[static_cast<size_t>(lo)] = o;
+    }
+    std::sort(off.begin(), off.end());
+    return static_cast<int>(std::unique(off.begin(), off.end()) - off.begin());
+}
+
 static const void *func_ptr(const util_state *s, int fid)
 {
     const Func &f = s->plan.funcs[fid];
@@ -615,11 +638,18 @@ int gpube_build_descriptors(util_state *s)
         x.n_lo = T.n_lo;
         x.n_gi = T.n_gi;
         // one global group input, at most 3 inputs, a fixed-domain variant:
-        // prefetch that input with the per-thread cp.async pipeline
+        // prefetch that input with the per-thread cp.async pipeline, unless
+        // a warp's lanes mostly read the same runs of it
         x.pipe = (!x.v4 && P.allow_pipe && x.F <= 3 && T.d >= 2 && T.d <= 8 && T.n_gi - T.n_lo == 1 && T.stage_off[T.n_lo] < 0 &&
                   T.G > 1)
                      ? 1
                      : 0;
+        if (x.pipe) {
+            std::vector<int32_t> st;
+            task_strides(w, P, T, st);
+            const int lanes = static_cast<int>(std::min<int64_t>(32, T.P_lo));
+            if (2 * warp_distinct_runs(w, T, st, T.n_lo, lanes) < lanes) x.pipe = 0;
+        }
         x.n_uo = T.n_uo;
         uint64_t sum_ub = 0;
         for (int fid : T.inputs) sum_ub += ub[fid];
