@@ -167,25 +167,35 @@ struct SumProduct : Cost<float> {
 };
 
 constexpr float kInfF = __builtin_huge_valf();
+
+__device__ __forceinline__ float min_of(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ uint32_t min_of(uint32_t a, uint32_t b) { return min(a, b); }
 // Factored sum-product rows below this sum of products are recomputed from
 // their raw terms (fp32 keeps full relative precision well above it).
 constexpr float kSfTiny = 1e-20f;
 
 // Elimination of one row's D sums: the first minimum and its index; for the
 // sum-product, -log sum exp(-acc[l]) taken relative to that minimum (every
-// exponent <= 0, one term is 1), +inf when every term is +inf.
-template <typename C, int D>
+// exponent <= 0, one term is 1), +inf when every term is +inf.  Where no
+// argmin is wanted (ARG = false, or the sum-product) the minimum is taken by
+// min instructions alone (the sums hold no NaN: costs are >= 0 or +inf).
+template <typename C, int D, bool ARG = true>
 __device__ __forceinline__ typename C::acc reduce_run(const typename C::acc (&acc)[D], int &bi)
 {
     using A = typename C::acc;
     A best = acc[0];
     bi = 0;
+    if constexpr (ARG && !C::kSum) {
 #pragma unroll
-    for (int l = 1; l < D; ++l)
-        if (acc[l] < best) {
-            best = acc[l];
-            bi = l;
-        }
+        for (int l = 1; l < D; ++l)
+            if (acc[l] < best) {
+                best = acc[l];
+                bi = l;
+            }
+    } else {
+#pragma unroll
+        for (int l = 1; l < D; ++l) best = min_of(best, acc[l]);
+    }
     if constexpr (C::kSum) {
         if (best < kInfF) {
             float t = 0.f;
@@ -384,7 +394,7 @@ __device__ __noinline__ void item_fixed_anyF(const TaskDev *__restrict__ tkp, co
                 for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
             }
             int bi;
-            const A best = reduce_run<C, D>(acc, bi);
+            const A best = reduce_run<C, D, WA>(acc, bi);
             const int o = Ar[0] + u * du[0] + lo;
             out[o] = C::store(best);
             if constexpr (!C::kSum && WA) tk.arg[o] = static_cast<uint8_t>(bi);
@@ -578,7 +588,7 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
 #pragma unroll
                             for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[u][j][r][l], k);
                         int bi;
-                        const A best = reduce_run<C, D>(acc, bi);
+                        const A best = reduce_run<C, D, WA>(acc, bi);
                         const int32_t o = oo[j] + u * d0;
                         out[o] = C::store(best);
                         if constexpr (!C::kSum && WA) arg[o] = static_cast<uint8_t>(bi);
@@ -600,7 +610,7 @@ __device__ __noinline__ void item_fixed_nr(const TaskDev *__restrict__ tkp, cons
                             for (int l = 0; l < D; ++l) acc[l] = C::add(acc[l], v[l], k);
                         }
                         int bi;
-                        const A best = reduce_run<C, D>(acc, bi);
+                        const A best = reduce_run<C, D, WA>(acc, bi);
                         out[oo[j]] = C::store(best);
                         if constexpr (!C::kSum && WA) arg[oo[j]] = static_cast<uint8_t>(bi);
                         oo[j] += d0;
@@ -754,12 +764,17 @@ __device__ __noinline__ void item_pipe(const TaskDev *__restrict__ tkp, const un
     auto reduce_store = [&](A (&acc)[D], int32_t o) {
         A best = acc[0];
         int bi = 0;
+        if constexpr (WA && !C::kSum) {
 #pragma unroll
-        for (int l = 1; l < D; ++l)
-            if (acc[l] < best) {
-                best = acc[l];
-                bi = l;
-            }
+            for (int l = 1; l < D; ++l)
+                if (acc[l] < best) {
+                    best = acc[l];
+                    bi = l;
+                }
+        } else {
+#pragma unroll
+            for (int l = 1; l < D; ++l) best = min_of(best, acc[l]);
+        }
         if constexpr (C::kSum) {
             if (best < kInfF) {
                 float t = 0.f;
@@ -1004,7 +1019,7 @@ __device__ __noinline__ void item_v4(const TaskDev *__restrict__ tkp, const unsi
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 int bb;
-                best[i] = C::store(reduce_run<C, D>(acc[i], bb));
+                best[i] = C::store(reduce_run<C, D, WA>(acc[i], bb));
                 bi |= static_cast<uint32_t>(bb) << (8 * i);
             }
             using V4 = typename std::conditional<std::is_same<T, float>::value, float4, int4>::type;
