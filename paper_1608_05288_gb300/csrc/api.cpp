@@ -666,6 +666,7 @@ int gpube_build_descriptors(util_state *s)
     s->launches.clear();
     s->launch_grid.clear();
     s->launch_smem.clear();
+    s->launch_ktype.clear();
     int32_t *counters = reinterpret_cast<int32_t *>(B + s->counters_off);
     int32_t *status = reinterpret_cast<int32_t *>(B + s->status_off);
     const int32_t *pre_dev = reinterpret_cast<const int32_t *>(B + D.prefix);
@@ -743,6 +744,11 @@ int gpube_build_descriptors(util_state *s)
         s->launches.push_back(L);
         s->launch_grid.push_back(static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(tot, cap))));
         s->launch_smem.push_back(smem);
+        // int32 launches whose tasks all take the packed-key rows of domain 4
+        // run the instantiation compiled with that item body alone
+        bool pk4 = s->ktype == kKTypeInt;
+        for (int i = 0; i < count && pk4; ++i) pk4 = task_is_pk4(td[first + i]);
+        s->launch_ktype.push_back(pk4 ? kKTypeIntPk4 : s->ktype);
         return GPUBE_OK;
     };
     s->n_zero = 1;
@@ -793,6 +799,7 @@ int gpube_build_descriptors(util_state *s)
         s->launches.push_back(L);
         s->launch_grid.push_back(static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(tot, cap))));
         s->launch_smem.push_back(smem);
+        s->launch_ktype.push_back(s->ktype);
         s->n_zero = static_cast<int32_t>(nt + 1);
     } else if (s->launch_mode == kLaunchPerLevel) {
         for (int l = 0; l < P.n_levels; ++l) {
@@ -1009,8 +1016,8 @@ int gpube_enqueue_util(util_state *s, cudaStream_t st)
     // consecutive levels: each launch may be scheduled while the previous one
     // drains (it waits for it before reading any table)
     for (size_t i = 0; i < s->launches.size(); ++i)
-        CUDA_TRY(launch_util(s->launches[i], s->ktype, s->launch_grid[i], s->cfg.threads, s->launch_smem[i],
-                             st, i > 0));
+        CUDA_TRY(launch_util(s->launches[i], s->launch_ktype[i], s->launch_grid[i], s->cfg.threads,
+                             s->launch_smem[i], st, i > 0));
     return GPUBE_OK;
 }
 
@@ -1066,6 +1073,7 @@ extern "C" int util_sync(util_state *s)
     int32_t status = 0;
     CUDA_TRY(cudaMemcpy(&status, s->base + s->status_off, 4, cudaMemcpyDeviceToHost));
     if (status == kStatusTimeout) return set_error(GPUBE_ETIMEDOUT, "a bounded device-side wait gave up");
+    if (status == kStatusBadSpec) return set_error(GPUBE_EINVAL, "internal: a task reached a specialised kernel");
     return GPUBE_OK;
 }
 
@@ -1150,6 +1158,7 @@ extern "C" int value_propagate(util_state *s, int32_t *assignment, solve_result 
     int32_t status;
     memcpy(&status, buf.data(), 4);
     if (status == kStatusTimeout) return set_error(GPUBE_ETIMEDOUT, "a bounded device-side wait gave up");
+    if (status == kStatusBadSpec) return set_error(GPUBE_EINVAL, "internal: a task reached a specialised kernel");
     const bool sum = kind_sum(s->plan.kind);  // no assignment, no Eq. 1 cost
     if (assignment && !sum) memcpy(assignment, buf.data() + 24, 4 * static_cast<size_t>(n));
     if (res) {

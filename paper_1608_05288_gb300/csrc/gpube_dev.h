@@ -15,12 +15,18 @@ constexpr unsigned long long kWaitNs = 1000000000ull;  // time limit of every de
 // Device status codes written to the status word.
 constexpr int kStatusOk = 0;
 constexpr int kStatusTimeout = 1;
+constexpr int kStatusBadSpec = 2;  // a task reached a specialised kernel it does not fit (host error)
 
 // UTIL kernel instantiations: int32 min-sum (WCSP_INT32_SAT), fp32 min-sum
 // (WCSP_FP32_LOG), fp32 sum-product
 constexpr int kKTypeInt = 0;
 constexpr int kKTypeFloat = 1;
 constexpr int kKTypeSum = 2;
+// int32 min-sum compiled with one item body only, the packed-key rows of
+// domain 4 with u of radix 4 (the full-size buckets of grid-like problems):
+// a launch whose tasks all take that body runs it, with its few hundred
+// instructions instead of the whole dispatch in the instruction caches
+constexpr int kKTypeIntPk4 = 3;
 
 // Kernel variants: the eliminated domain class times the input-count class.
 // D class 0 = any domain size (runtime loop, one thread per row); 1..9 =
@@ -91,6 +97,20 @@ struct alignas(16) TaskDev {
 };
 
 static_assert(sizeof(TaskDev) == 128, "a task descriptor is one 128-byte line");
+
+#if defined(__CUDACC__)
+#define GPUBE_HD __host__ __device__
+#else
+#define GPUBE_HD
+#endif
+
+// The task shape of the int32 instantiation specialised for the packed-key
+// rows of domain 4 (kKTypeIntPk4): the shape item_fixed<C, 4, 3> sends to
+// item_pipe<C, 4, 0, true, 4, true>.
+GPUBE_HD inline bool task_is_pk4(const TaskDev &t)
+{
+    return t.variant == 3 * kNumFClass && !t.v4 && t.pipe && t.R0 == 4 && t.F == t.n_uo && t.nosat;
+}
 
 // Depth of the per-thread cp.async pipeline of group inputs (groups ahead),
 // and the most groups one item of that path spans (its A rows are copied to

@@ -230,7 +230,7 @@ struct util_state {
     int num_sms = 0;
     // launches of one run
     std::vector<gpube::LaunchDev> launches;
-    std::vector<int32_t> launch_grid, launch_smem;
+    std::vector<int32_t> launch_grid, launch_smem, launch_ktype;
     // value plan pointers
     gpube::ValueDev vdev{};
     int32_t value_smem = 0;

@@ -1465,7 +1465,10 @@ __device__ __forceinline__ bool wait_producers(const LaunchDev &L, int a, unsign
 }
 
 // ------------------------------------------------------------- kernel
-template <typename C>
+// SPEC = 0: every variant (dispatch by the task's descriptor); SPEC = 1
+// (int32 only): the packed-key rows of domain 4 alone, for launches whose
+// tasks all take them (a task that does not fit sets kStatusBadSpec).
+template <typename C, int SPEC = 0>
 __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
 {
     extern __shared__ __align__(128) unsigned char stage[];
@@ -1614,9 +1617,19 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
         const bool wide = tk.variant / kNumFClass == kDClassWide;
         const int lo = wide ? lc * static_cast<int>(blockDim.x >> 5) + (tid >> 5)
                             : (lc * static_cast<int>(blockDim.x) + tid) * (tk.v4 ? 4 : 1);
-        if (lo < tk.P_lo)
-            dispatch<C>(L.tasks + a, tk, stage, stage + L.pipe_off, reinterpret_cast<const int32_t *>(stage + L.arows_off),
-                        lo, h0, h1, L.top_k);
+        if (lo < tk.P_lo) {
+            if constexpr (SPEC == 1) {
+                if (task_is_pk4(tk))
+                    item_pipe<C, 4, 0, true, 4, true>(L.tasks + a, stage, stage + L.pipe_off,
+                                                      reinterpret_cast<const int32_t *>(stage + L.arows_off), lo, h0,
+                                                      h1, L.top_k);
+                else
+                    atomicExch(L.status, kStatusBadSpec);
+            } else {
+                dispatch<C>(L.tasks + a, tk, stage, stage + L.pipe_off,
+                            reinterpret_cast<const int32_t *>(stage + L.arows_off), lo, h0, h1, L.top_k);
+            }
+        }
 
         __syncthreads();
         if (L.done != nullptr && tid == 0) {

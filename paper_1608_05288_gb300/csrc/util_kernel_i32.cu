@@ -9,10 +9,26 @@ cudaError_t launch_util_i32(const LaunchDev &L, int grid, int threads, int smem,
     return launch_util_kernel(util_kernel<Cost<int32_t>>, L, grid, threads, smem, s, pdl);
 }
 
+cudaError_t launch_util_i32_pk4(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl)
+{
+    return launch_util_kernel(util_kernel<Cost<int32_t>, 1>, L, grid, threads, smem, s, pdl);
+}
+
 int util_max_blocks_i32(int threads, int smem)
 {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, util_kernel<Cost<int32_t>>, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+int util_max_blocks_i32_pk4(int threads, int smem)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, util_kernel<Cost<int32_t>, 1>, threads, smem) !=
+        cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -36,6 +52,8 @@ cudaError_t launch_value_batch_i32(const ValueBatch &B, int smem, cudaStream_t s
 cudaError_t kernel_attrs_i32(int max_smem)
 {
     cudaError_t e = cudaFuncSetAttribute(util_kernel<Cost<int32_t>>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(util_kernel<Cost<int32_t>, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(value_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e == cudaSuccess)
