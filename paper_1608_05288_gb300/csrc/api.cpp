@@ -744,11 +744,12 @@ int gpube_build_descriptors(util_state *s)
         s->launches.push_back(L);
         s->launch_grid.push_back(static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(tot, cap))));
         s->launch_smem.push_back(smem);
-        // int32 launches whose tasks all take the packed-key rows of domain 4
-        // run the instantiation compiled with that item body alone
-        bool pk4 = s->ktype == kKTypeInt;
-        for (int i = 0; i < count && pk4; ++i) pk4 = task_is_pk4(td[first + i]);
-        s->launch_ktype.push_back(pk4 ? kKTypeIntPk4 : s->ktype);
+        // int32 and sum-product launches whose tasks all take the two-term
+        // rows of domain 4 run the instantiation compiled with that body alone
+        const bool pk = s->ktype == kKTypeInt;
+        bool rows4 = pk || s->ktype == kKTypeSum;
+        for (int i = 0; i < count && rows4; ++i) rows4 = task_is_rows4(td[first + i], pk);
+        s->launch_ktype.push_back(!rows4 ? s->ktype : pk ? kKTypeIntRows4 : kKTypeSumRows4);
         return GPUBE_OK;
     };
     s->n_zero = 1;

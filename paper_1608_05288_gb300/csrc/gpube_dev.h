@@ -22,11 +22,13 @@ constexpr int kStatusBadSpec = 2;  // a task reached a specialised kernel it doe
 constexpr int kKTypeInt = 0;
 constexpr int kKTypeFloat = 1;
 constexpr int kKTypeSum = 2;
-// int32 min-sum compiled with one item body only, the packed-key rows of
-// domain 4 with u of radix 4 (the full-size buckets of grid-like problems):
-// a launch whose tasks all take that body runs it, with its few hundred
+// The same instantiations compiled with one item body only, the two-term
+// rows of domain 4 with u of radix 4 (the full-size buckets of grid-like
+// problems; packed keys for int32, factored rows for the sum-product): a
+// launch whose tasks all take that body runs it, with its few hundred
 // instructions instead of the whole dispatch in the instruction caches
-constexpr int kKTypeIntPk4 = 3;
+constexpr int kKTypeIntRows4 = 3;
+constexpr int kKTypeSumRows4 = 4;
 
 // Kernel variants: the eliminated domain class times the input-count class.
 // D class 0 = any domain size (runtime loop, one thread per row); 1..9 =
@@ -104,12 +106,13 @@ static_assert(sizeof(TaskDev) == 128, "a task descriptor is one 128-byte line");
 #define GPUBE_HD
 #endif
 
-// The task shape of the int32 instantiation specialised for the packed-key
-// rows of domain 4 (kKTypeIntPk4): the shape item_fixed<C, 4, 3> sends to
-// item_pipe<C, 4, 0, true, 4, true>.
-GPUBE_HD inline bool task_is_pk4(const TaskDev &t)
+// The task shape of the instantiations specialised for the two-term rows of
+// domain 4 (kKTypeIntRows4, kKTypeSumRows4): the shape item_fixed<C, 4, 3>
+// sends to item_pipe<C, 4, 0, true, 4, packed> (packed: int32 sums below
+// the top cost, as packed keys).
+GPUBE_HD inline bool task_is_rows4(const TaskDev &t, bool packed)
 {
-    return t.variant == 3 * kNumFClass && !t.v4 && t.pipe && t.R0 == 4 && t.F == t.n_uo && t.nosat;
+    return t.variant == 3 * kNumFClass && !t.v4 && t.pipe && t.R0 == 4 && t.F == t.n_uo && (!packed || t.nosat);
 }
 
 // Depth of the per-thread cp.async pipeline of group inputs (groups ahead),

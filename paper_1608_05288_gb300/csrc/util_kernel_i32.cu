@@ -9,7 +9,7 @@ cudaError_t launch_util_i32(const LaunchDev &L, int grid, int threads, int smem,
     return launch_util_kernel(util_kernel<Cost<int32_t>>, L, grid, threads, smem, s, pdl);
 }
 
-cudaError_t launch_util_i32_pk4(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl)
+cudaError_t launch_util_i32_rows4(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl)
 {
     return launch_util_kernel(util_kernel<Cost<int32_t>, 1>, L, grid, threads, smem, s, pdl);
 }
@@ -24,7 +24,7 @@ int util_max_blocks_i32(int threads, int smem)
     return nb > 0 ? nb : 1;
 }
 
-int util_max_blocks_i32_pk4(int threads, int smem)
+int util_max_blocks_i32_rows4(int threads, int smem)
 {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, util_kernel<Cost<int32_t>, 1>, threads, smem) !=

@@ -11,6 +11,11 @@ cudaError_t launch_util_sum(const LaunchDev &L, int grid, int threads, int smem,
     return launch_util_kernel(util_kernel<SumProduct>, L, grid, threads, smem, s, pdl);
 }
 
+cudaError_t launch_util_sum_rows4(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl)
+{
+    return launch_util_kernel(util_kernel<SumProduct, 1>, L, grid, threads, smem, s, pdl);
+}
+
 int util_max_blocks_sum(int threads, int smem)
 {
     int nb = 0;
@@ -21,9 +26,22 @@ int util_max_blocks_sum(int threads, int smem)
     return nb > 0 ? nb : 1;
 }
 
+int util_max_blocks_sum_rows4(int threads, int smem)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, util_kernel<SumProduct, 1>, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
 cudaError_t kernel_attrs_sum(int max_smem)
 {
-    return cudaFuncSetAttribute(util_kernel<SumProduct>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    cudaError_t e = cudaFuncSetAttribute(util_kernel<SumProduct>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(util_kernel<SumProduct, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    return e;
 }
 
 }  // namespace gpube
