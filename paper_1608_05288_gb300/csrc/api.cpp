@@ -745,11 +745,13 @@ int gpube_build_descriptors(util_state *s)
         s->launch_grid.push_back(static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(tot, cap))));
         s->launch_smem.push_back(smem);
         // int32 and sum-product launches whose tasks all take the two-term
-        // rows of domain 4 run the instantiation compiled with that body alone
+        // rows of one domain D (2..4) run the instantiation compiled with
+        // that body alone
         const bool pk = s->ktype == kKTypeInt;
-        bool rows4 = pk || s->ktype == kKTypeSum;
-        for (int i = 0; i < count && rows4; ++i) rows4 = task_is_rows4(td[first + i], pk);
-        s->launch_ktype.push_back(!rows4 ? s->ktype : pk ? kKTypeIntRows4 : kKTypeSumRows4);
+        int rows_d = (pk || s->ktype == kKTypeSum) ? rows_spec_of(td[first], pk) : 0;
+        for (int i = 1; i < count && rows_d; ++i)
+            if (rows_spec_of(td[first + i], pk) != rows_d) rows_d = 0;
+        s->launch_ktype.push_back(rows_d ? (pk ? kKTypeIntRows : kKTypeSumRows) + rows_d - 2 : s->ktype);
         return GPUBE_OK;
     };
     s->n_zero = 1;

@@ -23,12 +23,13 @@ constexpr int kKTypeInt = 0;
 constexpr int kKTypeFloat = 1;
 constexpr int kKTypeSum = 2;
 // The same instantiations compiled with one item body only, the two-term
-// rows of domain 4 with u of radix 4 (the full-size buckets of grid-like
-// problems; packed keys for int32, factored rows for the sum-product): a
-// launch whose tasks all take that body runs it, with its few hundred
-// instructions instead of the whole dispatch in the instruction caches
-constexpr int kKTypeIntRows4 = 3;
-constexpr int kKTypeSumRows4 = 4;
+// rows of domain D with u of radix D, D = 2, 3, 4 (the full-size buckets of
+// grid-like problems; packed keys for int32, factored rows for the
+// sum-product): a launch whose tasks all take that body runs it, with its
+// few hundred instructions instead of the whole dispatch in the instruction
+// caches.  Kernel types kKTypeIntRows + D - 2 and kKTypeSumRows + D - 2.
+constexpr int kKTypeIntRows = 3;
+constexpr int kKTypeSumRows = 6;
 
 // Kernel variants: the eliminated domain class times the input-count class.
 // D class 0 = any domain size (runtime loop, one thread per row); 1..9 =
@@ -106,13 +107,17 @@ static_assert(sizeof(TaskDev) == 128, "a task descriptor is one 128-byte line");
 #define GPUBE_HD
 #endif
 
-// The task shape of the instantiations specialised for the two-term rows of
-// domain 4 (kKTypeIntRows4, kKTypeSumRows4): the shape item_fixed<C, 4, 3>
-// sends to item_pipe<C, 4, 0, true, 4, packed> (packed: int32 sums below
-// the top cost, as packed keys).
-GPUBE_HD inline bool task_is_rows4(const TaskDev &t, bool packed)
+// The domain D of the single-body instantiation that a task fits, or 0: the
+// tasks that item_fixed<C, D, 3> sends to item_pipe<C, D, 0, true, D,
+// packed> (domain class 1..3 = domain 2..4, at most 3 inputs, the group
+// input pipelined, u of radix D, no other per-row input; packed: int32 sums
+// below the top cost, as packed keys).
+GPUBE_HD inline int rows_spec_of(const TaskDev &t, bool packed)
 {
-    return t.variant == 3 * kNumFClass && !t.v4 && t.pipe && t.R0 == 4 && t.F == t.n_uo && (!packed || t.nosat);
+    const int D = t.variant / kNumFClass + 1;
+    if (t.variant % kNumFClass != 0 || D < 2 || D > 4) return 0;
+    if (t.v4 || !t.pipe || t.R0 != D || t.F != t.n_uo || (packed && !t.nosat)) return 0;
+    return D;
 }
 
 // Depth of the per-thread cp.async pipeline of group inputs (groups ahead),

@@ -14,13 +14,13 @@ namespace gpube {
 cudaError_t launch_util_i32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl);
 cudaError_t launch_util_f32(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl);
 cudaError_t launch_util_sum(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl);
-cudaError_t launch_util_i32_rows4(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl);
-cudaError_t launch_util_sum_rows4(const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl);
+cudaError_t launch_util_i32_rows(int D, const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl);
+cudaError_t launch_util_sum_rows(int D, const LaunchDev &L, int grid, int threads, int smem, cudaStream_t s, bool pdl);
 int util_max_blocks_i32(int threads, int smem);
 int util_max_blocks_f32(int threads, int smem);
 int util_max_blocks_sum(int threads, int smem);
-int util_max_blocks_i32_rows4(int threads, int smem);
-int util_max_blocks_sum_rows4(int threads, int smem);
+int util_max_blocks_i32_rows(int D, int threads, int smem);
+int util_max_blocks_sum_rows(int D, int threads, int smem);
 cudaError_t launch_value_i32(const ValueDev &V, int smem, cudaStream_t s);
 cudaError_t launch_value_f32(const ValueDev &V, int smem, cudaStream_t s);
 cudaError_t launch_value_batch_i32(const ValueBatch &B, int smem, cudaStream_t s);
@@ -131,15 +131,17 @@ cudaError_t launch_selftest_wait(int32_t *status, unsigned long long limit_ns, c
 
 // -------------------------------------------------------- host launchers
 // ktype: kKTypeInt (int32 min-sum), kKTypeFloat (fp32 min-sum), kKTypeSum
-// (fp32 sum-product), kKTypeIntRows4 / kKTypeSumRows4 (the same, two-term rows
-// of domain 4 only)
+// (fp32 sum-product), kKTypeIntRows + D - 2 / kKTypeSumRows + D - 2 (the
+// same, two-term rows of domain D = 2..4 only)
 cudaError_t launch_util(const LaunchDev &L, int ktype, int grid, int threads, int smem, cudaStream_t s, bool pdl)
 {
+    if (ktype >= kKTypeIntRows && ktype < kKTypeIntRows + 3)
+        return launch_util_i32_rows(ktype - kKTypeIntRows + 2, L, grid, threads, smem, s, pdl);
+    if (ktype >= kKTypeSumRows && ktype < kKTypeSumRows + 3)
+        return launch_util_sum_rows(ktype - kKTypeSumRows + 2, L, grid, threads, smem, s, pdl);
     switch (ktype) {
     case kKTypeFloat: return launch_util_f32(L, grid, threads, smem, s, pdl);
     case kKTypeSum: return launch_util_sum(L, grid, threads, smem, s, pdl);
-    case kKTypeIntRows4: return launch_util_i32_rows4(L, grid, threads, smem, s, pdl);
-    case kKTypeSumRows4: return launch_util_sum_rows4(L, grid, threads, smem, s, pdl);
     default: return launch_util_i32(L, grid, threads, smem, s, pdl);
     }
 }
@@ -159,12 +161,16 @@ int util_max_blocks_per_sm(int ktype, int threads, int smem)
         if (it != cache.end()) return it->second;
     }
     int nb;
-    switch (ktype) {
-    case kKTypeFloat: nb = util_max_blocks_f32(threads, smem); break;
-    case kKTypeSum: nb = util_max_blocks_sum(threads, smem); break;
-    case kKTypeIntRows4: nb = util_max_blocks_i32_rows4(threads, smem); break;
-    case kKTypeSumRows4: nb = util_max_blocks_sum_rows4(threads, smem); break;
-    default: nb = util_max_blocks_i32(threads, smem); break;
+    if (ktype >= kKTypeIntRows && ktype < kKTypeIntRows + 3) {
+        nb = util_max_blocks_i32_rows(ktype - kKTypeIntRows + 2, threads, smem);
+    } else if (ktype >= kKTypeSumRows && ktype < kKTypeSumRows + 3) {
+        nb = util_max_blocks_sum_rows(ktype - kKTypeSumRows + 2, threads, smem);
+    } else {
+        switch (ktype) {
+        case kKTypeFloat: nb = util_max_blocks_f32(threads, smem); break;
+        case kKTypeSum: nb = util_max_blocks_sum(threads, smem); break;
+        default: nb = util_max_blocks_i32(threads, smem); break;
+        }
     }
     std::lock_guard<std::mutex> g(mu);
     cache[key] = nb;

@@ -1465,10 +1465,10 @@ __device__ __forceinline__ bool wait_producers(const LaunchDev &L, int a, unsign
 }
 
 // ------------------------------------------------------------- kernel
-// SPEC = 0: every variant (dispatch by the task's descriptor); SPEC = 1
-// (int32 and the sum-product): the two-term rows of domain 4 alone, for
-// launches whose tasks all take them (a task that does not fit sets
-// kStatusBadSpec).
+// SPEC = 0: every variant (dispatch by the task's descriptor); SPEC = D
+// (2..4; int32 and the sum-product): the two-term rows of domain D with u of
+// radix D alone, for launches whose tasks all take them (a task that does
+// not fit sets kStatusBadSpec).
 template <typename C, int SPEC = 0>
 __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
 {
@@ -1619,12 +1619,12 @@ __global__ void __launch_bounds__(kMaxThreads, 2) util_kernel(const LaunchDev L)
         const int lo = wide ? lc * static_cast<int>(blockDim.x >> 5) + (tid >> 5)
                             : (lc * static_cast<int>(blockDim.x) + tid) * (tk.v4 ? 4 : 1);
         if (lo < tk.P_lo) {
-            if constexpr (SPEC == 1) {
+            if constexpr (SPEC > 0) {
                 constexpr bool kPk = std::is_same<C, Cost<int32_t>>::value;
-                if (task_is_rows4(tk, kPk))
-                    item_pipe<C, 4, 0, true, 4, kPk>(L.tasks + a, stage, stage + L.pipe_off,
-                                                     reinterpret_cast<const int32_t *>(stage + L.arows_off), lo, h0,
-                                                     h1, L.top_k);
+                if (rows_spec_of(tk, kPk) == SPEC)
+                    item_pipe<C, SPEC, 0, true, SPEC, kPk>(L.tasks + a, stage, stage + L.pipe_off,
+                                                           reinterpret_cast<const int32_t *>(stage + L.arows_off), lo,
+                                                           h0, h1, L.top_k);
                 else
                     atomicExch(L.status, kStatusBadSpec);
             } else {
